@@ -1,0 +1,164 @@
+"""Python access to the FP64 CPU oracle (``nurbs_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: imported by the test suite, by the smoke check and by
+the CPU-baseline leg of the benchmark.  The product path never imports it.  It
+shares no code with the CUDA library.
+
+Each function takes numpy arrays, widens them to float64 (exact for the FP32
+inputs the GPU path sees) and calls the C routine of the same role:
+
+* ``find_span``, ``basis_funs``        -- span search and nonzero basis (Sec. 3.1 steps 1-2)
+* ``basis_cox_de_boor``               -- brute-force recursion, Eq. 4 / Eq. 5
+* ``basis_knot_jac``                  -- knot Jacobian of the nonzero basis (Sec. 3.2)
+* ``surface_eval`` / ``curve_eval``   -- Eq. 3 (and its one-direction form)
+* ``surface_vjp`` / ``curve_vjp``     -- Eq. 7, Eq. 8, Eq. 9 + knot derivative
+* ``mse``, ``adam``                   -- the L2 (MSE) loss and the Adam step of Sec. 4
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "nurbs_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "libnurbs_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+_D = ctypes.POINTER(ctypes.c_double)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc into oracle/_build (plain C, no CUDA)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = ctypes.CDLL(build())
+            i, d, sz = ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+            L.nurbs_oracle_find_span.argtypes = [i, i, d, _D]
+            L.nurbs_oracle_find_span.restype = i
+            L.nurbs_oracle_basis_funs.argtypes = [i, d, i, _D, _D]
+            L.nurbs_oracle_basis_cox_de_boor.argtypes = [i, i, d, _D, i]
+            L.nurbs_oracle_basis_cox_de_boor.restype = d
+            L.nurbs_oracle_basis_knot_jac.argtypes = [i, d, i, _D, _D, _D]
+            L.nurbs_oracle_surface_eval.argtypes = [i, i, i, i, _D, _D, _D, i, _D, i, _D, _D]
+            L.nurbs_oracle_surface_vjp.argtypes = [i, i, i, i, _D, _D, _D, i, _D, i, _D, _D, _D, _D, _D]
+            L.nurbs_oracle_curve_eval.argtypes = [i, i, _D, _D, i, _D, _D]
+            L.nurbs_oracle_curve_vjp.argtypes = [i, i, _D, _D, i, _D, _D, _D, _D]
+            L.nurbs_oracle_mse.argtypes = [sz, _D, _D, d, _D]
+            L.nurbs_oracle_mse.restype = d
+            L.nurbs_oracle_adam.argtypes = [sz, _D, _D, _D, _D, i, d, d, d, d]
+            _lib = L
+    return _lib
+
+
+def _f64(x) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(x, dtype=np.float64))
+
+
+def _p(a: np.ndarray | None):
+    return None if a is None else a.ctypes.data_as(_D)
+
+
+# --------------------------------------------------------------------- basis
+def find_span(n: int, p: int, u: float, U) -> int:
+    U = _f64(U)
+    return int(lib().nurbs_oracle_find_span(n, p, float(u), _p(U)))
+
+
+def basis_funs(span: int, u: float, p: int, U) -> np.ndarray:
+    U = _f64(U)
+    N = np.zeros(p + 1)
+    lib().nurbs_oracle_basis_funs(span, float(u), p, _p(U), _p(N))
+    return N
+
+
+def basis_cox_de_boor(i: int, p: int, u: float, U) -> float:
+    U = _f64(U)
+    return float(lib().nurbs_oracle_basis_cox_de_boor(i, p, float(u), _p(U), len(U)))
+
+
+def basis_knot_jac(span: int, u: float, p: int, U):
+    """(N[p+1], dN[p+1, 2p]) with dN[r, k] = dN_{span-p+r}/dU[span-p+1+k]."""
+    U = _f64(U)
+    N = np.zeros(p + 1)
+    dN = np.zeros((p + 1) * max(2 * p, 1))
+    lib().nurbs_oracle_basis_knot_jac(span, float(u), p, _p(U), _p(N), _p(dN))
+    return N, dN.reshape(p + 1, max(2 * p, 1))[:, : 2 * p]
+
+
+# ------------------------------------------------------------------- surface
+def surface_eval(p, q, U, V, ctrl, u, v) -> np.ndarray:
+    """ctrl: [n1, m1, 4] (x, y, z, w).  Returns S[nu, nv, 3] in float64."""
+    ctrl = _f64(ctrl)
+    n1, m1 = ctrl.shape[0], ctrl.shape[1]
+    U, V, u, v = _f64(U), _f64(V), _f64(u), _f64(v)
+    assert len(U) == n1 + p + 1 and len(V) == m1 + q + 1
+    out = np.zeros((len(u), len(v), 3))
+    lib().nurbs_oracle_surface_eval(p, q, n1, m1, _p(U), _p(V), _p(ctrl), len(u), _p(u), len(v), _p(v), _p(out))
+    return out
+
+
+def surface_vjp(p, q, U, V, ctrl, u, v, g, want_ctrl=True, want_knots=True):
+    """Returns (dctrl[n1, m1, 4], dU, dV); entries not requested are None."""
+    ctrl = _f64(ctrl)
+    n1, m1 = ctrl.shape[0], ctrl.shape[1]
+    U, V, u, v, g = _f64(U), _f64(V), _f64(u), _f64(v), _f64(g)
+    assert g.shape == (len(u), len(v), 3)
+    dctrl = np.zeros((n1, m1, 4)) if want_ctrl else None
+    dU = np.zeros(len(U)) if want_knots else None
+    dV = np.zeros(len(V)) if want_knots else None
+    lib().nurbs_oracle_surface_vjp(p, q, n1, m1, _p(U), _p(V), _p(ctrl), len(u), _p(u), len(v), _p(v),
+                                   _p(g), _p(dctrl), _p(dU), _p(dV))
+    return dctrl, dU, dV
+
+
+# --------------------------------------------------------------------- curve
+def curve_eval(p, U, ctrl, u) -> np.ndarray:
+    ctrl = _f64(ctrl)
+    n1 = ctrl.shape[0]
+    U, u = _f64(U), _f64(u)
+    assert len(U) == n1 + p + 1
+    out = np.zeros((len(u), 3))
+    lib().nurbs_oracle_curve_eval(p, n1, _p(U), _p(ctrl), len(u), _p(u), _p(out))
+    return out
+
+
+def curve_vjp(p, U, ctrl, u, g, want_ctrl=True, want_knots=True):
+    ctrl = _f64(ctrl)
+    n1 = ctrl.shape[0]
+    U, u, g = _f64(U), _f64(u), _f64(g)
+    dctrl = np.zeros((n1, 4)) if want_ctrl else None
+    dU = np.zeros(len(U)) if want_knots else None
+    lib().nurbs_oracle_curve_vjp(p, n1, _p(U), _p(ctrl), len(u), _p(u), _p(g), _p(dctrl), _p(dU))
+    return dctrl, dU
+
+
+# ----------------------------------------------------------------- loss, adam
+def mse(S, T, count: float):
+    """(L, g): L = sum (S-T)^2 / count, g = 2 (S-T) / count."""
+    S, T = _f64(S), _f64(T)
+    g = np.zeros_like(S)
+    L = lib().nurbs_oracle_mse(S.size, _p(S), _p(T), float(count), _p(g))
+    return float(L), g
+
+
+def adam(theta, g, m, v, t: int, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+    """One Adam step; returns updated copies (theta, m, v)."""
+    theta, g, m, v = _f64(theta).copy(), _f64(g), _f64(m).copy(), _f64(v).copy()
+    lib().nurbs_oracle_adam(theta.size, _p(theta), _p(g), _p(m), _p(v), int(t), lr, b1, b2, eps)
+    return theta, m, v
