@@ -1,0 +1,347 @@
+"""Throughput benchmark of the NURBS-Diff hot path on GB300.
+
+Workload (one step): a batch of 256 bicubic NURBS surfaces, 32x32 control nets,
+clamped random knots (28 sorted U[0,1] interior knots per direction, every gap
+>= 1e-3), weights U[0.5, 2], a 128x128 uniform (u, v) grid; forward evaluation,
+MSE against a seeded target surface and the backward pass with gradients for
+control points, weights and knots -- all in one libnurbs launch
+(nurbs_mse_fwd_bwd).  Metric: surface points per second, forward + backward.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun every rank runs its own replica of the batch (weak scaling, no
+collective on the data path); rank 0 prints one JSON line.
+
+--impl reference times the FP64 CPU oracle (the correctness reference of the
+tests) on a bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOAD = {"workload": "256 bicubic NURBS surfaces, 32x32 control nets, random clamped knots, 128x128 grid, "
+                        "fwd + MSE + bwd (dP, dw, dU, dV)",
+            "batch": 256, "p": 3, "q": 3, "net": 32, "grid": 128}
+METRIC = "surface pts/s fwd+bwd FP32"
+
+
+def algorithmic_bytes(npts: int, descs) -> int:
+    """Bytes the method must move for one fwd+MSE+bwd step.
+
+    Per point: the target read (12 B) and the evaluated point written (12 B).
+    Per item: the control net read and its gradient written (16 B per control
+    point each), knots read and their gradient written (4 B each), the samples
+    read (4 B each) and the item's loss written (4 B).
+    """
+    b = 24 * npts
+    for d in descs:
+        nc = int(d["n1"]) * int(d["m1"])
+        nk = int(d["n1"] + d["p"] + 1) + int(d["m1"] + d["q"] + 1)
+        b += 32 * nc + 8 * nk + 4 * (int(d["nu"]) + int(d["nv"])) + 4
+    return b
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_workload(device):
+    import torch
+
+    from paper_2104_14547_gb300 import batch, synth
+    surfs, targets = synth.bicubic_batch(0, WORKLOAD["batch"], WORKLOAD["net"], WORKLOAD["grid"])
+    pk = batch.pack_surfaces(surfs)
+    tk = batch.pack_surfaces(targets)
+    plan = batch.Plan.for_packed(pk, device=device)
+    kn, ct, pr = batch.to_device(pk, device)
+    # the target surface: the forward of an independent control net on the same knots and grid
+    tplan = batch.Plan.for_packed(tk, device=device)
+    _, tct, _ = batch.to_device(tk, device)
+    target = torch.empty((pk.npts, 3), device=device)
+    tplan.eval(kn, tct, pr, target)
+    torch.cuda.synchronize(device)
+    return pk, plan, kn, ct, pr, target
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2104_14547_gb300 import batch
+
+    pk, plan, kn, ct, pr, target = make_workload(dev)
+    npts = pk.npts
+    pts = torch.empty((npts, 3), device=dev)
+    gc = torch.empty_like(ct)
+    gk = torch.empty_like(kn)
+    loss = torch.empty(pk.count, device=dev)
+    scale = 2.0 / (3.0 * npts)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)   # > L2 (129 MB)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        plan.mse_fwd_bwd(kn, ct, pr, target, pts, gc, gk, loss, scale)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    st, flags = plan.get_error()
+    assert st == 0, (st, flags)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    for k in range(args.steps):
+        flush.zero_()                     # L2 flushed before every timed step
+        starts[k].record(stream)
+        step()
+        ends[k].record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    t_ms = float(np.sum(ms))
+    if world > 1:
+        tt = torch.tensor([t_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        dist.barrier()
+        t_ms = float(tt.item())
+    ms_per_step = t_ms / args.steps
+    value = world * npts * args.steps / (t_ms / 1e3)
+
+    # roofline of the one kernel of the step (the fused forward+backward tile kernel)
+    abytes = algorithmic_bytes(npts, pk.descs)
+    achieved = abytes / (ms_per_step / 1e3) / 1e9
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    traffic = None
+    try:
+        prof = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+        traffic = prof.get("fused_mse_fwd_bwd_cfg2_bytes_per_launch")
+    except Exception:
+        pass
+
+    # end to end through the public API: pinned host inputs in, loss + gradients out
+    h_target = target.cpu().pin_memory()
+    h_ctrl = ct.cpu().pin_memory()
+    h_knots = kn.cpu().pin_memory()
+    h_params = pr.cpu().pin_memory()
+    h_gc = torch.empty_like(gc, device="cpu").pin_memory()
+    h_gk = torch.empty_like(gk, device="cpu").pin_memory()
+    h_loss = torch.empty_like(loss, device="cpu").pin_memory()
+    bi = sum(t.numel() * t.element_size() for t in (h_target, h_ctrl, h_knots, h_params))
+    bo = sum(t.numel() * t.element_size() for t in (h_gc, h_gk, h_loss))
+
+    def e2e_step():
+        target.copy_(h_target, non_blocking=True)
+        ct.copy_(h_ctrl, non_blocking=True)
+        kn.copy_(h_knots, non_blocking=True)
+        pr.copy_(h_params, non_blocking=True)
+        step()
+        h_gc.copy_(gc, non_blocking=True)
+        h_gk.copy_(gk, non_blocking=True)
+        h_loss.copy_(loss, non_blocking=True)
+
+    for _ in range(max(1, args.warmup)):
+        e2e_step()
+    torch.cuda.synchronize(dev)
+    e_ms = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        e2e_step()
+        e1.record(stream)
+        e1.synchronize()
+        e_ms += e0.elapsed_time(e1)
+    if world > 1:
+        tt = torch.tensor([e_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e_ms = float(tt.item())
+    e2e_value = world * npts * args.steps / (e_ms / 1e3)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(budget_s=args.cpu_seconds)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "pts/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded, shapes of the paper's fitting workloads)",
+            "config": dict(WORKLOAD, l2_flush="256 MiB write before every timed step", parallelism=f"replicas{world}",
+                           points_per_step=npts * world),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic, "algorithmic_bytes": abytes,
+                         "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy)" if peaks else "fallback 6.8 TB/s",
+                         "kernel": "tiles_kernel<3,3,grad,knots> (nurbs_mse_fwd_bwd)"},
+            "e2e": {"value": e2e_value, "unit": "pts/s", "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo},
+            "gpu_launches": args.steps * len(set(zip(pk.descs["p"], pk.descs["q"]))),
+            "clocks": clk,
+        }
+        if cpu is not None:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def cpu_baseline(budget_s: float = 15.0):
+    """The FP64 oracle, as it is, on the host: forward + MSE + VJP of whole
+    surfaces of the benchmark workload, one after another, for about budget_s
+    seconds of timed work (the target evaluation is not timed)."""
+    from oracle import oracle as O
+    from paper_2104_14547_gb300 import synth
+    surfs, targets = synth.bicubic_batch(0, WORKLOAD["batch"], WORKLOAD["net"], WORKLOAD["grid"])
+    total = WORKLOAD["batch"] * WORKLOAD["grid"] ** 2
+    done_pts, work_s, k = 0, 0.0, 0
+    while k < len(surfs) and work_s < budget_s:
+        s, t = surfs[k], targets[k]
+        T = O.surface_eval(t.p, t.q, t.U, t.V, t.ctrl, t.u, t.v)
+        ts = time.perf_counter()
+        S = O.surface_eval(s.p, s.q, s.U, s.V, s.ctrl, s.u, s.v)
+        _, g = O.mse(S, T, 3 * total)
+        O.surface_vjp(s.p, s.q, s.U, s.V, s.ctrl, s.u, s.v, g)
+        work_s += time.perf_counter() - ts
+        done_pts += s.npts
+        k += 1
+    return {"value": done_pts / work_s, "unit": "pts/s", "cores": 1, "kind": "oracle",
+            "sample": f"{k} of {WORKLOAD['batch']} surfaces ({done_pts} points), fwd + MSE + VJP incl. knots, FP64"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    from paper_2104_14547_gb300 import synth
+    surfs, targets = synth.bicubic_batch(0, WORKLOAD["batch"], WORKLOAD["net"], WORKLOAD["grid"])
+    total = WORKLOAD["batch"] * WORKLOAD["grid"] ** 2
+    per_step = 2   # surfaces per step: a bounded sample of the workload
+    Ts = [O.surface_eval(t.p, t.q, t.U, t.V, t.ctrl, t.u, t.v) for t in targets[: per_step * (args.steps + args.warmup)]]
+
+    def step(k):
+        pts = 0
+        for j in range(per_step):
+            idx = k * per_step + j
+            s = surfs[idx % len(surfs)]
+            S = O.surface_eval(s.p, s.q, s.U, s.V, s.ctrl, s.u, s.v)
+            _, g = O.mse(S, Ts[idx % len(Ts)], 3 * total)
+            O.surface_vjp(s.p, s.q, s.U, s.V, s.ctrl, s.u, s.v, g)
+            pts += s.npts
+        return pts
+
+    for k in range(args.warmup):
+        step(k)
+    t0 = time.perf_counter()
+    pts = 0
+    for k in range(args.steps):
+        pts += step(args.warmup + k)
+    secs = time.perf_counter() - t0
+    value = pts / secs
+    line = {"metric": METRIC, "value": value, "unit": "pts/s", "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded)", "impl": "reference",
+            "config": dict(WORKLOAD, sample_per_step=f"{per_step} surfaces"),
+            "cpu_baseline": {"value": value, "unit": "pts/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{per_step} of {WORKLOAD['batch']} surfaces per step"},
+            "e2e": {"value": value, "unit": "pts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

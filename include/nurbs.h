@@ -1,0 +1,207 @@
+/*
+ * libnurbs -- GB300 (sm_103a) kernels for the data-parallel hot path of NURBS-Diff
+ * (Prasad et al., arXiv 2104.14547): batched evaluation of rational B-spline
+ * curves and surfaces on sample grids and its backward pass.
+ *
+ * Conventions for every entry point below
+ * ---------------------------------------
+ * - Pointers named d_* (and every float array argument of an execution call) are
+ *   DEVICE pointers owned by the caller; h_* are host pointers.  The library never
+ *   frees or retains caller memory beyond the call, and execution calls allocate
+ *   no device memory: all scratch lives in a caller-provided workspace.
+ * - Execution calls are asynchronous on the given stream (a cudaStream_t; NULL is
+ *   the legacy default stream).  They return after the launch; device-side data
+ *   errors are reported through nurbs_plan_get_error().
+ * - All arithmetic is FP32.  Layouts are row-major, u the slow index.
+ * - Calls sharing one workspace must not overlap on the GPU (they share counters
+ *   and partial-sum slots).
+ *
+ * Data layout (packed, ragged batch)
+ * ----------------------------------
+ *   knots[]   float   each item's U (n1+p+1 floats) and V (m1+q+1) at desc offsets
+ *   ctrl[]    float4  each item's control net [n1][m1] of (x, y, z, w): the
+ *                     Cartesian control point P_ij and its weight w_ij (Eq. 3);
+ *                     the offset must make the address 16-byte aligned
+ *   params[]  float   each item's u samples (nu) and v samples (nv),
+ *                     non-decreasing, inside [U_p, U_{n+1}] and [V_q, V_{m+1}]
+ *   pts[]     float   each item's output block [nu][nv][3] at desc.pts * 3
+ * Gradients use the layouts of the arrays they differentiate: grad_ctrl[] is a
+ * float4 array (dL/dx, dL/dy, dL/dz, dL/dw) at the ctrl offsets; grad_knots[] is
+ * a float array at the knot offsets.
+ * A curve is an item with one parametric direction: p = its degree, n1 = its
+ * control-point count, nu = its sample count; q, m1, nv, knot_v and param_v are
+ * ignored.  Its output block is [nu][3].
+ */
+#ifndef NURBS_H
+#define NURBS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ABI-identical to cudaStream_t. */
+typedef struct CUstream_st* nurbs_stream_t;
+
+typedef enum nurbs_status {
+    NURBS_OK = 0,
+    NURBS_ERR_ARG = 1,          /* NULL pointer, negative or zero size, bad kind / flag */
+    NURBS_ERR_KNOTS = 2,        /* device check: knots decreasing, or first/last span empty */
+    NURBS_ERR_DEGREE = 3,       /* degree outside [1, NURBS_MAX_DEGREE] or fewer than p+1 control points */
+    NURBS_ERR_DOMAIN = 4,       /* device check: a sample outside [U_p, U_{n+1}] */
+    NURBS_ERR_ORDER = 5,        /* device check: samples not non-decreasing */
+    NURBS_ERR_WORKSPACE = 6,    /* workspace NULL, too small, misaligned, or plan not bound */
+    NURBS_ERR_CUDA = 7,         /* a CUDA runtime call failed (see nurbs_last_cuda_error) */
+    NURBS_ERR_SIZE = 8,         /* an item exceeds a kernel limit (control net, offsets) */
+    NURBS_ERR_KIND = 9          /* the plan was built for the other kind (curve vs surface) */
+} nurbs_status;
+
+#define NURBS_MAX_DEGREE 5
+#define NURBS_MAX_CTRL 4096     /* control points per direction */
+
+enum { NURBS_KIND_SURFACE = 0, NURBS_KIND_CURVE = 1 };
+
+/* One item (surface or curve) of a packed batch.  Offsets are element offsets
+ * into the arrays named in the layout note above. */
+typedef struct nurbs_desc {
+    int32_t p, q;        /* degrees */
+    int32_t n1, m1;      /* control points per direction (n+1, m+1) */
+    int32_t nu, nv;      /* sample counts per direction */
+    int32_t reserved0, reserved1;
+    int64_t knot_u;      /* offset of U in knots[] (floats) */
+    int64_t knot_v;      /* offset of V in knots[] (floats) */
+    int64_t ctrl;        /* offset of the control net in ctrl[] (float4 elements) */
+    int64_t param_u;     /* offset of the u samples in params[] (floats) */
+    int64_t param_v;     /* offset of the v samples in params[] (floats) */
+    int64_t pts;         /* offset of the output block in pts[] (points, 3 floats each) */
+} nurbs_desc;
+
+/* Tile shape for a plan.  Zero fields take the library's defaults. */
+typedef struct nurbs_tile_cfg {
+    int32_t rows;        /* sample rows per tile (surfaces) / samples per tile (curves) */
+    int32_t warps;       /* warps per CTA (1..16) */
+    int32_t ctas_per_sm; /* persistent CTAs per SM (0 = as many as fit) */
+    int32_t reserved;
+} nurbs_tile_cfg;
+
+/* Adam hyper-parameters (Kingma & Ba; the optimiser of Sec. 4). */
+typedef struct nurbs_adam {
+    float lr, beta1, beta2, eps;
+} nurbs_adam;
+
+typedef struct nurbs_plan nurbs_plan;
+
+/*
+ * nurbs_plan_create -- split a batch into tiles (host only, no GPU work).
+ *   kind      NURBS_KIND_SURFACE or NURBS_KIND_CURVE
+ *   h_desc    host array of `count` descriptors (copied; may be freed afterwards)
+ *   cfg       tile shape, or NULL for defaults
+ *   out       receives the plan; release with nurbs_plan_destroy
+ * Errors: NURBS_ERR_ARG, NURBS_ERR_DEGREE, NURBS_ERR_SIZE.  Sizes only are
+ * checked here; knot and sample values are checked on the device.
+ */
+nurbs_status nurbs_plan_create(int32_t kind, const nurbs_desc* h_desc, int32_t count,
+                               const nurbs_tile_cfg* cfg, nurbs_plan** out);
+
+/* Bytes of device workspace the plan needs (256-byte aligned pointer required). */
+size_t nurbs_plan_workspace_size(const nurbs_plan* plan);
+
+/* Points (samples) the plan evaluates, summed over items. */
+int64_t nurbs_plan_points(const nurbs_plan* plan);
+
+/* Tiles the plan launches and the CTAs of one launch (for reporting). */
+int32_t nurbs_plan_tiles(const nurbs_plan* plan);
+int32_t nurbs_plan_ctas(const nurbs_plan* plan);
+
+/*
+ * nurbs_plan_bind -- attach a device workspace to the plan: uploads the item and
+ * tile tables and zeroes the counters and the error word (async on `stream`; the
+ * host tables are staged in plan-owned host memory that stays valid until the
+ * plan is destroyed).  Must precede any execution call with this plan, and be
+ * repeated if the workspace pointer changes.
+ * Errors: NURBS_ERR_ARG, NURBS_ERR_WORKSPACE, NURBS_ERR_CUDA.
+ */
+nurbs_status nurbs_plan_bind(nurbs_plan* plan, void* d_workspace, size_t bytes, nurbs_stream_t stream);
+
+void nurbs_plan_destroy(nurbs_plan* plan);
+
+/*
+ * nurbs_plan_get_error -- synchronise `stream`, read and clear the device error
+ * word written by the device-side checks of earlier calls.  *flags receives the
+ * raw bit set (bit k set <=> status k was raised); returns the lowest raised
+ * status, or NURBS_OK.
+ */
+nurbs_status nurbs_plan_get_error(nurbs_plan* plan, nurbs_stream_t stream, uint32_t* flags);
+
+/*
+ * nurbs_eval_surface -- forward evaluation of every surface item (Eq. 3,
+ * Sec. 3.1 steps 1-3, Alg. 1): span search, nonzero Cox-de Boor basis (Eq. 4),
+ * homogeneous weighted sum and perspective divide, S(u_a, v_b) -> pts.
+ */
+nurbs_status nurbs_eval_surface(const nurbs_plan* plan, const float* knots, const float* ctrl,
+                                const float* params, float* pts, nurbs_stream_t stream);
+
+/* nurbs_eval_curve -- the same for curve items (Sec. 3, curves). */
+nurbs_status nurbs_eval_curve(const nurbs_plan* plan, const float* knots, const float* ctrl,
+                              const float* params, float* pts, nurbs_stream_t stream);
+
+/*
+ * nurbs_backward -- vector-Jacobian product of the evaluation (Sec. 3.2, Eq. 7,
+ * Eq. 8, Eq. 9, the knot derivative, Alg. 2), for surface or curve plans.
+ *   grad_pts    dL/dS in the pts layout
+ *   grad_ctrl   receives (dL/dx, dL/dy, dL/dz, dL/dw) per control point, or NULL
+ *   grad_knots  receives dL/dU (and dL/dV), or NULL.  Knot gradients are the
+ *               almost-everywhere derivative of the Cox-de Boor recursion (the
+ *               sigma -> 0 limit of the smoothed indicator of Sec. 3.2); the
+ *               p+1 knots at each end of a knot vector receive 0.
+ * Outputs are overwritten, not accumulated.  Basis values are recomputed, not
+ * stored by the forward call.
+ */
+nurbs_status nurbs_backward(const nurbs_plan* plan, const float* knots, const float* ctrl,
+                            const float* params, const float* grad_pts, float* grad_ctrl,
+                            float* grad_knots, nurbs_stream_t stream);
+
+/*
+ * nurbs_mse_fwd_bwd -- forward, MSE loss against `target` (pts layout) and the
+ * backward of that loss in one launch (the L2 loss of Sec. 4 read as a mean
+ * squared error, Eq. 1 chain rule).
+ *   pts         receives S, or NULL to skip the write
+ *   loss_items  receives each item's sum of squared differences (float[count]), or NULL
+ *   grad_scale  dL/dS = grad_scale * (S - T); 2 / (3 * total points) gives the
+ *               gradient of the mean over all coordinates
+ * grad_ctrl / grad_knots as in nurbs_backward (either may be NULL).
+ */
+nurbs_status nurbs_mse_fwd_bwd(const nurbs_plan* plan, const float* knots, const float* ctrl,
+                               const float* params, const float* target, float* pts,
+                               float* grad_ctrl, float* grad_knots, float* loss_items,
+                               float grad_scale, nurbs_stream_t stream);
+
+/*
+ * nurbs_fit_step -- one fused fitting step: forward, MSE against `target`,
+ * backward, and an Adam update (Sec. 4, Eq. 13 with Adam) of every control point
+ * and weight in place.  Knots are not updated.
+ *   ctrl        control nets, updated in place
+ *   adam_m/v    Adam moments, float4 per control point in the ctrl layout (zero
+ *               before the first step), updated in place
+ *   step        1-based Adam step number (bias correction)
+ *   pts, loss_items, grad_knots  as in nurbs_mse_fwd_bwd (NULL to skip)
+ */
+nurbs_status nurbs_fit_step(const nurbs_plan* plan, const float* knots, float* ctrl,
+                            const float* params, const float* target, float* pts,
+                            float* adam_m, float* adam_v, const nurbs_adam* hp, int32_t step,
+                            float grad_scale, float* loss_items, float* grad_knots,
+                            nurbs_stream_t stream);
+
+/* Human-readable name of a status code (static string). */
+const char* nurbs_status_string(nurbs_status status);
+
+/* The last CUDA runtime error code seen by the library on this thread (0 = none). */
+int32_t nurbs_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NURBS_H */

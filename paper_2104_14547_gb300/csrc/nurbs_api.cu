@@ -1,0 +1,448 @@
+// C-ABI of libnurbs: planning (tiling a ragged batch, workspace layout),
+// binding a workspace, and the execution entry points declared in nurbs.h.
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/nurbs.h"
+#include "nurbs_kernel.cuh"
+
+using namespace nurbs;
+
+namespace {
+
+thread_local int32_t g_last_cuda_error = 0;
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+inline int align4(int x) { return (x + 3) & ~3; }
+
+nurbs_status cuda_fail(cudaError_t e)
+{
+    g_last_cuda_error = (int32_t)e;
+    return NURBS_ERR_CUDA;
+}
+
+}  // namespace
+
+struct PlanGroup {
+    int p, q;         // internal degrees (p == 0 for curves)
+    int t0, t1;       // tile range
+    int grid[3];      // CTAs per launch for forward / backward / backward + knots (0 = unknown)
+};
+
+struct nurbs_plan {
+    int32_t kind;
+    int32_t warps;            // warps per CTA
+    int32_t ctas_per_sm;      // 0 = occupancy limit
+    std::vector<ItemDev> items;
+    std::vector<TileDev> tiles;
+    int64_t points;
+    // shared memory carve-up
+    int R, C, acc_cap;
+    int off_misc, off_su, off_u, off_nu, off_sv, off_v, off_nv, off_stage, off_beta, off_duc, off_dvc, off_acc;
+    int smem_bytes;
+    // workspace layout (bytes)
+    size_t items_off, tiles_off, counts_off, part_off, ws_bytes;
+    // binding
+    void* ws;
+    size_t ws_len;
+    std::vector<unsigned char> staging;   // host image of the tables (kept alive for async copies)
+    std::vector<PlanGroup> groups;        // one kernel launch per (p, q) group
+};
+
+namespace {
+
+nurbs_status check_desc(int32_t kind, const nurbs_desc& d)
+{
+    if (d.nu < 0 || d.n1 <= 0) return NURBS_ERR_ARG;
+    if (d.p < 1 || d.p > NURBS_MAX_DEGREE || d.n1 < d.p + 1) return NURBS_ERR_DEGREE;
+    if (d.n1 > NURBS_MAX_CTRL) return NURBS_ERR_SIZE;
+    if (d.knot_u < 0 || d.ctrl < 0 || d.param_u < 0 || d.pts < 0) return NURBS_ERR_ARG;
+    if (kind == NURBS_KIND_SURFACE) {
+        if (d.nv < 0 || d.m1 <= 0) return NURBS_ERR_ARG;
+        if (d.q < 1 || d.q > NURBS_MAX_DEGREE || d.m1 < d.q + 1) return NURBS_ERR_DEGREE;
+        if (d.m1 > NURBS_MAX_CTRL) return NURBS_ERR_SIZE;
+        if (d.knot_v < 0 || d.param_v < 0) return NURBS_ERR_ARG;
+    }
+    return NURBS_OK;
+}
+
+// Internal item: a curve is a surface with a degree-0, single-row u direction.
+ItemDev make_item(int32_t kind, const nurbs_desc& d)
+{
+    ItemDev it;
+    std::memset(&it, 0, sizeof it);
+    if (kind == NURBS_KIND_CURVE) {
+        it.p = 0; it.q = d.p; it.n1 = 1; it.m1 = d.n1; it.nu = d.nu > 0 ? 1 : 0; it.nv = d.nu;
+        it.knot_u = 0; it.knot_v = d.knot_u; it.ctrl = d.ctrl;
+        it.param_u = 0; it.param_v = d.param_u; it.pts = d.pts; it.curve = 1;
+    } else {
+        it.p = d.p; it.q = d.q; it.n1 = d.n1; it.m1 = d.m1; it.nu = d.nu; it.nv = d.nv;
+        it.knot_u = d.knot_u; it.knot_v = d.knot_v; it.ctrl = d.ctrl;
+        it.param_u = d.param_u; it.param_v = d.param_v; it.pts = d.pts; it.curve = 0;
+    }
+    return it;
+}
+
+}  // namespace
+
+extern "C" {
+
+nurbs_status nurbs_plan_create(int32_t kind, const nurbs_desc* h_desc, int32_t count,
+                               const nurbs_tile_cfg* cfg, nurbs_plan** out)
+{
+    if (out == nullptr) return NURBS_ERR_ARG;
+    *out = nullptr;
+    if (kind != NURBS_KIND_SURFACE && kind != NURBS_KIND_CURVE) return NURBS_ERR_ARG;
+    if (count < 0 || (count > 0 && h_desc == nullptr)) return NURBS_ERR_ARG;
+    for (int32_t k = 0; k < count; ++k) {
+        nurbs_status st = check_desc(kind, h_desc[k]);
+        if (st != NURBS_OK) return st;
+    }
+    nurbs_plan* pl = new (std::nothrow) nurbs_plan();
+    if (pl == nullptr) return NURBS_ERR_ARG;
+    pl->kind = kind;
+    pl->warps = 8;
+    pl->ctas_per_sm = 0;
+    int rows_cfg = 0;
+    if (cfg != nullptr) {
+        if (cfg->warps < 0 || cfg->warps > 8 || cfg->rows < 0 || cfg->ctas_per_sm < 0) { delete pl; return NURBS_ERR_ARG; }
+        if (cfg->warps > 0) pl->warps = cfg->warps;
+        rows_cfg = cfg->rows;
+        pl->ctas_per_sm = cfg->ctas_per_sm;
+    }
+    const int NW = pl->warps;
+    const int maxcols = 32 * NW;
+    pl->points = 0;
+    pl->items.reserve(count);
+    int maxR = 1, maxC = 32, max_m1 = 1;
+    long long part_floats = 0;
+    for (int32_t k = 0; k < count; ++k) {
+        ItemDev it = make_item(kind, h_desc[k]);
+        pl->points += (int64_t)it.nu * it.nv;
+        max_m1 = std::max(max_m1, it.m1);
+        pl->items.push_back(it);
+    }
+    // tiles, grouped by degree pair so that each group runs one specialised kernel
+    for (int g = 0; g < kMaxGroups; ++g) {
+        const int gp = g / 5, gq = g % 5 + 1;
+        PlanGroup grp;
+        grp.p = gp; grp.q = gq;
+        grp.t0 = (int)pl->tiles.size();
+        grp.grid[0] = grp.grid[1] = grp.grid[2] = 0;
+        for (int32_t k = 0; k < count; ++k) {
+            ItemDev& it = pl->items[k];
+            if (it.p != gp || it.q != gq) continue;
+            it.first_tile = (int)pl->tiles.size();
+            // column tiles of at most 32*NW samples; row tiles of R rows split into row groups
+            const int nct = std::max(1, (it.nv + maxcols - 1) / maxcols);
+            const int cw = it.nv > 0 ? ((it.nv + nct - 1) / nct + 31) / 32 * 32 : 32;
+            const int nwc = std::max(1, std::min(NW, cw / 32));
+            int nwr = it.curve ? 1 : std::max(1, NW / nwc);
+            int R = it.curve ? 1 : (rows_cfg > 0 ? rows_cfg : 16 * nwr);
+            nwr = std::min(nwr, R);
+            const int nrt = std::max(1, (it.nu + R - 1) / R);
+            const int rpg_full = (R + nwr - 1) / nwr;
+            it.rcap = std::min(it.n1, rpg_full * (it.p + 1));
+            it.ku_cap = it.curve ? 0 : it.n1 + it.p + 1;
+            it.kv_cap = it.m1 + it.q + 1;
+            it.wbase = align4(12 + it.ku_cap + it.kv_cap);
+            it.abase = align4(4 + it.rcap);
+            it.warp_slot = it.abase + 4 * it.rcap * it.m1;
+            int ntl = 0;
+            for (int rt = 0; rt < nrt; ++rt) {
+                for (int ct = 0; ct < nct; ++ct) {
+                    TileDev tl;
+                    std::memset(&tl, 0, sizeof tl);
+                    tl.item = k;
+                    tl.row0 = rt * R;
+                    tl.nrows = std::max(0, std::min(R, it.nu - tl.row0));
+                    tl.col0 = ct * cw;
+                    tl.ncols = std::max(0, std::min(cw, it.nv - tl.col0));
+                    tl.tidx = ntl++;
+                    tl.nwc = nwc;
+                    tl.nwr = nwr;
+                    tl.rpg = std::max(1, (tl.nrows + nwr - 1) / nwr);
+                    tl.part = part_floats;
+                    part_floats += it.wbase + (long long)nwc * nwr * it.warp_slot;
+                    part_floats = (part_floats + 63) / 64 * 64;   // 256-byte aligned slots
+                    pl->tiles.push_back(tl);
+                    maxR = std::max(maxR, tl.nrows);
+                    maxC = std::max(maxC, nwc * 32);
+                }
+            }
+            it.ntiles = ntl;
+        }
+        grp.t1 = (int)pl->tiles.size();
+        if (grp.t1 > grp.t0) pl->groups.push_back(grp);
+    }
+    // shared memory carve-up for the largest tile
+    pl->R = maxR;
+    pl->C = maxC;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 16); return (int)o; };
+    pl->off_misc = take(256);
+    pl->off_su = take(4 * maxR);
+    pl->off_u = take(4 * maxR);
+    pl->off_nu = take(4 * maxR * kMaxBasis);
+    pl->off_sv = take(4 * maxC);
+    pl->off_v = take(4 * maxC);
+    pl->off_nv = take(4 * maxC * kMaxBasis);
+    pl->off_stage = take(16 * 32 * NW);
+    pl->off_beta = take(4 * NW * maxR * kMaxBasis);
+    pl->off_duc = take(4 * maxR * kMaxKnotWin);
+    pl->off_dvc = take(4 * NW * 32 * kMaxKnotWin);
+    pl->off_acc = pl->off_su;     // the final reduction reuses the tile tables
+    const size_t min_acc = 16 * (size_t)std::max(1024, max_m1);
+    if (off < (size_t)pl->off_acc + min_acc) off = pl->off_acc + min_acc;
+    pl->acc_cap = (int)((off - pl->off_acc) / 16);
+    pl->smem_bytes = (int)off;
+    // workspace layout
+    size_t w = kHeaderBytes;
+    pl->items_off = w; w = align_up(w + sizeof(ItemDev) * pl->items.size(), 256);
+    pl->tiles_off = w; w = align_up(w + sizeof(TileDev) * pl->tiles.size(), 256);
+    pl->counts_off = w; w = align_up(w + 4 * pl->items.size(), 256);
+    pl->part_off = w; w = align_up(w + 4 * (size_t)part_floats, 256);
+    pl->ws_bytes = w;
+    pl->ws = nullptr;
+    pl->ws_len = 0;
+    *out = pl;
+    return NURBS_OK;
+}
+
+size_t nurbs_plan_workspace_size(const nurbs_plan* plan) { return plan ? plan->ws_bytes : 0; }
+int64_t nurbs_plan_points(const nurbs_plan* plan) { return plan ? plan->points : 0; }
+int32_t nurbs_plan_tiles(const nurbs_plan* plan) { return plan ? (int32_t)plan->tiles.size() : 0; }
+
+void nurbs_plan_destroy(nurbs_plan* plan) { delete plan; }
+
+nurbs_status nurbs_plan_bind(nurbs_plan* pl, void* d_ws, size_t bytes, nurbs_stream_t stream)
+{
+    if (pl == nullptr) return NURBS_ERR_ARG;
+    if (d_ws == nullptr || bytes < pl->ws_bytes || ((uintptr_t)d_ws & 255u) != 0) return NURBS_ERR_WORKSPACE;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    pl->staging.assign(pl->part_off, 0);
+    std::memcpy(pl->staging.data() + pl->items_off, pl->items.data(), sizeof(ItemDev) * pl->items.size());
+    std::memcpy(pl->staging.data() + pl->tiles_off, pl->tiles.data(), sizeof(TileDev) * pl->tiles.size());
+    cudaError_t e = cudaMemcpyAsync(d_ws, pl->staging.data(), pl->part_off, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(e);
+    pl->ws = d_ws;
+    pl->ws_len = bytes;
+    return NURBS_OK;
+}
+
+nurbs_status nurbs_plan_get_error(nurbs_plan* pl, nurbs_stream_t stream, uint32_t* flags)
+{
+    if (pl == nullptr) return NURBS_ERR_ARG;
+    if (pl->ws == nullptr) return NURBS_ERR_WORKSPACE;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    uint32_t word = 0;
+    cudaError_t e = cudaMemcpyAsync(&word, pl->ws, 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(pl->ws, 0, 4, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (flags) *flags = word;
+    for (int b = 1; b < 32; ++b)
+        if (word & (1u << b)) return (nurbs_status)b;
+    return NURBS_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+KernelVariant variant_for(int v, int p, int q)
+{
+    switch (p) {
+        case 0: return variant_p0(v, q);
+        case 1: return variant_p1(v, q);
+        case 2: return variant_p2(v, q);
+        case 3: return variant_p3(v, q);
+        case 4: return variant_p4(v, q);
+        default: return variant_p5(v, q);
+    }
+}
+
+// Launch variant v (0 forward, 1 backward, 2 backward + knots): one persistent
+// kernel per degree group, in group order on `s`.
+nurbs_status launch(const nurbs_plan* cpl, int v, KParams& kp, cudaStream_t s)
+{
+    nurbs_plan* pl = const_cast<nurbs_plan*>(cpl);
+    if (pl->ws == nullptr) return NURBS_ERR_WORKSPACE;
+    if (pl->tiles.empty()) return NURBS_OK;
+    unsigned char* ws = static_cast<unsigned char*>(pl->ws);
+    kp.items = reinterpret_cast<const ItemDev*>(ws + pl->items_off);
+    kp.tiles = reinterpret_cast<const TileDev*>(ws + pl->tiles_off);
+    kp.hdr = reinterpret_cast<WsHeader*>(ws);
+    kp.counts = reinterpret_cast<unsigned int*>(ws + pl->counts_off);
+    kp.part = reinterpret_cast<float*>(ws + pl->part_off);
+    kp.R = pl->R; kp.C = pl->C;
+    kp.off_misc = pl->off_misc; kp.off_su = pl->off_su; kp.off_u = pl->off_u; kp.off_nu = pl->off_nu;
+    kp.off_sv = pl->off_sv; kp.off_v = pl->off_v; kp.off_nv = pl->off_nv; kp.off_stage = pl->off_stage;
+    kp.off_beta = pl->off_beta; kp.off_duc = pl->off_duc; kp.off_dvc = pl->off_dvc; kp.off_acc = pl->off_acc;
+    kp.acc_cap = pl->acc_cap;
+    const int block = 32 * pl->warps;
+    for (PlanGroup& grp : pl->groups) {
+        KernelVariant kv = variant_for(v, grp.p, grp.q);
+        if (grp.grid[v] == 0) {
+            cudaError_t e = cudaSuccess;
+            if (pl->smem_bytes > 48 * 1024) e = kv.set_smem(pl->smem_bytes);
+            if (e != cudaSuccess) return cuda_fail(e);
+            int occ = 0;
+            e = kv.occupancy(&occ, block, pl->smem_bytes);
+            if (e != cudaSuccess) return cuda_fail(e);
+            int dev = 0, sms = 0;
+            e = cudaGetDevice(&dev);
+            if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            if (e != cudaSuccess) return cuda_fail(e);
+            if (occ < 1) return NURBS_ERR_SIZE;
+            if (pl->ctas_per_sm > 0) occ = std::min(occ, pl->ctas_per_sm);
+            grp.grid[v] = std::max(1, std::min(grp.t1 - grp.t0, occ * sms));
+        }
+        kp.t0 = grp.t0;
+        kp.t1 = grp.t1;
+        kp.queue = kp.hdr->queue + 2 * (grp.p * 5 + grp.q - 1);
+        cudaError_t e = kv.launch(kp, grp.grid[v], block, pl->smem_bytes, s);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    return NURBS_OK;
+}
+
+void zero_params(KParams& kp)
+{
+    std::memset(&kp, 0, sizeof kp);
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t nurbs_plan_ctas(const nurbs_plan* plan)
+{
+    if (plan == nullptr) return 0;
+    int n = 0;
+    for (const PlanGroup& g : plan->groups) n += std::max(g.grid[0], std::max(g.grid[1], g.grid[2]));
+    return n;
+}
+
+static nurbs_status eval_common(const nurbs_plan* pl, int32_t kind, const float* knots, const float* ctrl,
+                                const float* params, float* pts, nurbs_stream_t stream)
+{
+    if (pl == nullptr) return NURBS_ERR_ARG;
+    if (pl->kind != kind) return NURBS_ERR_KIND;
+    if (pl->tiles.empty()) return NURBS_OK;
+    if (knots == nullptr || ctrl == nullptr || params == nullptr || pts == nullptr) return NURBS_ERR_ARG;
+    if (((uintptr_t)ctrl & 15u) != 0) return NURBS_ERR_ARG;
+    KParams kp;
+    zero_params(kp);
+    kp.knots = knots;
+    kp.ctrl = reinterpret_cast<const float4*>(ctrl);
+    kp.params = params;
+    kp.pts = pts;
+    return launch(pl, 0, kp, reinterpret_cast<cudaStream_t>(stream));
+}
+
+nurbs_status nurbs_eval_surface(const nurbs_plan* plan, const float* knots, const float* ctrl,
+                                const float* params, float* pts, nurbs_stream_t stream)
+{
+    return eval_common(plan, NURBS_KIND_SURFACE, knots, ctrl, params, pts, stream);
+}
+
+nurbs_status nurbs_eval_curve(const nurbs_plan* plan, const float* knots, const float* ctrl,
+                              const float* params, float* pts, nurbs_stream_t stream)
+{
+    return eval_common(plan, NURBS_KIND_CURVE, knots, ctrl, params, pts, stream);
+}
+
+static nurbs_status grad_common(const nurbs_plan* pl, const float* knots, const float* ctrl, float* ctrl_w,
+                                const float* params, const float* gin, int gsrc, float* pts,
+                                float* grad_ctrl, float* grad_knots, float* loss_items, float grad_scale,
+                                float* adam_m, float* adam_v, const nurbs_adam* hp, int32_t step,
+                                nurbs_stream_t stream)
+{
+    if (pl == nullptr) return NURBS_ERR_ARG;
+    if (pl->tiles.empty()) return NURBS_OK;
+    if (knots == nullptr || ctrl == nullptr || params == nullptr || gin == nullptr) return NURBS_ERR_ARG;
+    if (((uintptr_t)ctrl & 15u) != 0 || ((uintptr_t)grad_ctrl & 15u) != 0) return NURBS_ERR_ARG;
+    KParams kp;
+    zero_params(kp);
+    kp.knots = knots;
+    kp.ctrl = reinterpret_cast<const float4*>(ctrl);
+    kp.ctrl_w = reinterpret_cast<float4*>(ctrl_w);
+    kp.params = params;
+    kp.pts = pts;
+    kp.gin = gin;
+    kp.gsrc = gsrc;
+    kp.grad_ctrl = reinterpret_cast<float4*>(grad_ctrl);
+    kp.grad_knots = grad_knots;
+    kp.loss_items = loss_items;
+    kp.grad_scale = grad_scale;
+    if (hp != nullptr) {
+        if (adam_m == nullptr || adam_v == nullptr || ctrl_w == nullptr || step < 1) return NURBS_ERR_ARG;
+        if (((uintptr_t)adam_m & 15u) != 0 || ((uintptr_t)adam_v & 15u) != 0) return NURBS_ERR_ARG;
+        const double bc1 = 1.0 - std::pow((double)hp->beta1, (double)step);
+        const double bc2 = 1.0 - std::pow((double)hp->beta2, (double)step);
+        kp.fit = 1;
+        kp.adam_m = reinterpret_cast<float4*>(adam_m);
+        kp.adam_v = reinterpret_cast<float4*>(adam_v);
+        kp.lr_t = (float)(hp->lr / bc1);
+        kp.inv_sqrt_bc2 = (float)(1.0 / std::sqrt(bc2));
+        kp.b1 = hp->beta1;
+        kp.b2 = hp->beta2;
+        kp.eps = hp->eps;
+    }
+    return launch(pl, grad_knots != nullptr ? 2 : 1, kp, reinterpret_cast<cudaStream_t>(stream));
+}
+
+nurbs_status nurbs_backward(const nurbs_plan* plan, const float* knots, const float* ctrl,
+                            const float* params, const float* grad_pts, float* grad_ctrl,
+                            float* grad_knots, nurbs_stream_t stream)
+{
+    return grad_common(plan, knots, ctrl, nullptr, params, grad_pts, 0, nullptr, grad_ctrl, grad_knots,
+                       nullptr, 0.f, nullptr, nullptr, nullptr, 0, stream);
+}
+
+nurbs_status nurbs_mse_fwd_bwd(const nurbs_plan* plan, const float* knots, const float* ctrl,
+                               const float* params, const float* target, float* pts,
+                               float* grad_ctrl, float* grad_knots, float* loss_items,
+                               float grad_scale, nurbs_stream_t stream)
+{
+    return grad_common(plan, knots, ctrl, nullptr, params, target, 1, pts, grad_ctrl, grad_knots,
+                       loss_items, grad_scale, nullptr, nullptr, nullptr, 0, stream);
+}
+
+nurbs_status nurbs_fit_step(const nurbs_plan* plan, const float* knots, float* ctrl,
+                            const float* params, const float* target, float* pts,
+                            float* adam_m, float* adam_v, const nurbs_adam* hp, int32_t step,
+                            float grad_scale, float* loss_items, float* grad_knots,
+                            nurbs_stream_t stream)
+{
+    if (hp == nullptr) return NURBS_ERR_ARG;
+    return grad_common(plan, knots, ctrl, ctrl, params, target, 1, pts, nullptr, grad_knots,
+                       loss_items, grad_scale, adam_m, adam_v, hp, step, stream);
+}
+
+const char* nurbs_status_string(nurbs_status s)
+{
+    switch (s) {
+        case NURBS_OK: return "ok";
+        case NURBS_ERR_ARG: return "invalid argument";
+        case NURBS_ERR_KNOTS: return "knot vector not non-decreasing or last span empty";
+        case NURBS_ERR_DEGREE: return "degree out of range or too few control points";
+        case NURBS_ERR_DOMAIN: return "sample outside the parametric domain";
+        case NURBS_ERR_ORDER: return "samples not non-decreasing";
+        case NURBS_ERR_WORKSPACE: return "workspace missing, too small, misaligned or not bound";
+        case NURBS_ERR_CUDA: return "CUDA runtime error";
+        case NURBS_ERR_SIZE: return "item exceeds a kernel limit";
+        case NURBS_ERR_KIND: return "plan built for the other kind";
+    }
+    return "unknown status";
+}
+
+int32_t nurbs_last_cuda_error(void) { return g_last_cuda_error; }
+
+}  // extern "C"

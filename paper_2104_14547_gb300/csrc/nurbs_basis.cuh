@@ -1,0 +1,105 @@
+// Device building blocks shared by the libnurbs kernels: knot-span search,
+// nonzero Cox-de Boor basis and its reverse-mode knot derivative.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace nurbs {
+
+// Knot-span search (Sec. 3.1 step 1): the largest k in [p, n] with U[k] <= u,
+// and n when u >= U[n+1].  Half-open spans, so a zero-length span is never
+// returned.  U is read through the read-only cache.
+__device__ __forceinline__ int find_span(int n, int p, float u, const float* __restrict__ U)
+{
+    if (u >= __ldg(U + n + 1)) return n;
+    int lo = p, hi = n;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (__ldg(U + mid) <= u) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// The P+1 nonzero basis functions N_{s-P..s}^P(u) of Eq. 4, evaluated with the
+// triangular scheme (each level from the previous one; the denominators
+// U_{s+r+1} - U_{s+1-j+r} are positive on a non-empty span).
+template <int P>
+__device__ __forceinline__ void basis_funs(int s, float u, const float* __restrict__ U, float (&N)[P + 1])
+{
+    N[0] = 1.f;
+    if constexpr (P > 0) {
+        float left[P + 1], right[P + 1];
+#pragma unroll
+        for (int j = 1; j <= P; ++j) {
+            left[j] = u - __ldg(U + s + 1 - j);
+            right[j] = __ldg(U + s + j) - u;
+            float saved = 0.f;
+#pragma unroll
+            for (int r = 0; r < j; ++r) {
+                float temp = N[r] / (right[r + 1] + left[j - r]);
+                N[r] = fmaf(right[r + 1], temp, saved);
+                saved = left[j - r] * temp;
+            }
+            N[j] = saved;
+        }
+    }
+}
+
+// Reverse-mode derivative of basis_funs with respect to the knots (the knot
+// derivative of Sec. 3.2 in its sigma -> 0 reading: the degree-0 indicators
+// contribute nothing, every coefficient of Eq. 4 is differentiated).
+// Given the cotangent nb[r] = dL/dN_{s-P+r}(u), writes
+//   dk[k] = sum_r nb[r] * dN_{s-P+r}(u) / dU[s-P+1+k],  k = 0 .. 2P-1.
+template <int P>
+__device__ __forceinline__ void basis_knot_vjp(int s, float u, const float* __restrict__ U,
+                                               const float (&nb_in)[P + 1], float (&dk)[2 * P + 1])
+{
+    if constexpr (P == 0) {
+        dk[0] = 0.f;
+    } else {
+        float left[P + 1], right[P + 1];
+        float tri[P + 1][P + 1];  // tri[j][r] = N^j_{s-j+r}
+        tri[0][0] = 1.f;
+#pragma unroll
+        for (int j = 1; j <= P; ++j) {
+            left[j] = u - __ldg(U + s + 1 - j);
+            right[j] = __ldg(U + s + j) - u;
+            float saved = 0.f;
+#pragma unroll
+            for (int r = 0; r < j; ++r) {
+                float temp = tri[j - 1][r] / (right[r + 1] + left[j - r]);
+                tri[j][r] = fmaf(right[r + 1], temp, saved);
+                saved = left[j - r] * temp;
+            }
+            tri[j][j] = saved;
+        }
+        float nb[P + 1], lb[P + 1], rb[P + 1];
+#pragma unroll
+        for (int r = 0; r <= P; ++r) { nb[r] = nb_in[r]; lb[r] = 0.f; rb[r] = 0.f; }
+#pragma unroll
+        for (int j = P; j >= 1; --j) {
+            float pb[P + 1];
+#pragma unroll
+            for (int r = 0; r < j; ++r) {
+                float den = right[r + 1] + left[j - r];
+                float temp = tri[j - 1][r] / den;
+                // temp feeds tri[j][r] (times right[r+1]) and tri[j][r+1] (times left[j-r])
+                float tb = fmaf(right[r + 1], nb[r], left[j - r] * nb[r + 1]);
+                float denb = -tb * temp / den;
+                rb[r + 1] += fmaf(temp, nb[r], denb);
+                lb[j - r] += fmaf(temp, nb[r + 1], denb);
+                pb[r] = tb / den;
+            }
+#pragma unroll
+            for (int r = 0; r < j; ++r) nb[r] = pb[r];
+        }
+        // left[j] = u - U[s+1-j]  -> knot index s+1-j = (s-P+1) + (P-j)
+        // right[j] = U[s+j] - u   -> knot index s+j   = (s-P+1) + (P-1+j)
+#pragma unroll
+        for (int j = 1; j <= P; ++j) {
+            dk[P - j] = -lb[j];
+            dk[P - 1 + j] = rb[j];
+        }
+    }
+}
+
+}  // namespace nurbs

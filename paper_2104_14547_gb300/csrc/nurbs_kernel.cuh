@@ -1,0 +1,66 @@
+// Persistent tile kernel, one instantiation per (u degree, v degree, variant):
+// CTAs pull tiles of their degree group from a queue in the workspace.
+#pragma once
+#include "nurbs_tile.cuh"
+
+namespace nurbs {
+
+template <int P, int Q, bool GRAD, bool KNOTS>
+__global__ void __launch_bounds__(256, 2) tiles_kernel(const __grid_constant__ KParams kp)
+{
+    __shared__ int s_t;
+    for (;;) {
+        if (threadIdx.x == 0) s_t = kp.t0 + (int)atomicAdd(kp.queue, 1u);
+        __syncthreads();
+        const int t = s_t;
+        __syncthreads();
+        if (t >= kp.t1) break;
+        tile_body<P, Q, GRAD, KNOTS>(kp, t);
+    }
+    // the last CTA out rearms the queue for the next launch on this workspace
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned e = atomicAdd(kp.queue + 1, 1u);
+        if (e + 1 == gridDim.x) {
+            kp.queue[0] = 0u;
+            kp.queue[1] = 0u;
+            __threadfence();
+        }
+    }
+}
+
+// Host-side hooks of one compiled kernel.
+struct KernelVariant {
+    cudaError_t (*launch)(const KParams&, int grid, int block, int smem, cudaStream_t);
+    cudaError_t (*occupancy)(int* ctas_per_sm, int block, int smem);
+    cudaError_t (*set_smem)(int smem);
+};
+
+template <int P, int Q, bool G, bool K>
+struct VariantOf {
+    static cudaError_t launch(const KParams& kp, int grid, int block, int smem, cudaStream_t s)
+    {
+        tiles_kernel<P, Q, G, K><<<grid, block, smem, s>>>(kp);
+        return cudaGetLastError();
+    }
+    static cudaError_t occupancy(int* n, int block, int smem)
+    {
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, tiles_kernel<P, Q, G, K>, block, smem);
+    }
+    static cudaError_t set_smem(int smem)
+    {
+        return cudaFuncSetAttribute(tiles_kernel<P, Q, G, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    }
+    static KernelVariant get() { return KernelVariant{launch, occupancy, set_smem}; }
+};
+
+// variant: 0 forward, 1 backward, 2 backward with knot gradients.
+// Defined per u degree in k_p<P>.cu.
+KernelVariant variant_p0(int v, int q);
+KernelVariant variant_p1(int v, int q);
+KernelVariant variant_p2(int v, int q);
+KernelVariant variant_p3(int v, int q);
+KernelVariant variant_p4(int v, int q);
+KernelVariant variant_p5(int v, int q);
+
+}  // namespace nurbs

@@ -1,0 +1,54 @@
+// Device-side tables of a bound plan (shared by the host planner and the
+// kernels).  Everything lives in the caller's workspace:
+//
+//   [0, 256)           WsHeader: error word, one persistent-queue pair per degree group
+//   items_off          ItemDev[count]
+//   tiles_off          TileDev[ntiles]
+//   counts_off         uint32 per item: tiles finished in the current launch
+//   part_off           partial-sum slots (floats), one per tile (see below)
+//
+// Tile slot (float offsets from TileDev::part):
+//   [0..7]    int: ku_lo, nku, kv_lo, nkv, valid, -, -, -
+//   [8]       float: loss (sum of squared differences over the tile)
+//   [12..)    dU partial (ku_cap floats), then dV partial (kv_cap floats)
+//   wbase     warp slots, one per warp of the CTA (ItemDev::warp_slot floats each):
+//               [0..3] int: rows stored, jlo, CW, valid
+//               [4..)  int: the control-row index of each stored row
+//               abase  float4 A[rows stored][m1]: homogeneous adjoint partial
+#pragma once
+#include <stdint.h>
+
+namespace nurbs {
+
+constexpr int kHeaderBytes = 256;
+
+constexpr int kMaxGroups = 30;   // distinct (p, q) pairs: p in 0..5, q in 1..5
+
+struct WsHeader {
+    unsigned int error;                  // bit k set <=> nurbs_status k raised on the device
+    unsigned int pad0;
+    unsigned int queue[2 * kMaxGroups];  // per degree group: next tile, CTAs finished
+    unsigned int pad1[2];
+};
+
+struct ItemDev {
+    int p, q, n1, m1, nu, nv;
+    int first_tile, ntiles;
+    int rcap;        // capacity of stored control rows per warp slot
+    int ku_cap, kv_cap;
+    int wbase;       // float offset of the first warp slot inside a tile slot
+    int warp_slot;   // floats per warp slot
+    int abase;       // float offset of A inside a warp slot (16-byte aligned)
+    int curve;       // 1: a curve item mapped onto the v direction (p == 0, n1 == 1)
+    int pad;
+    long long knot_u, knot_v, ctrl, param_u, param_v, pts;
+};
+
+struct TileDev {
+    int item, row0, nrows, col0, ncols, tidx;
+    int nwc, nwr, rpg;   // column warps, row groups, rows per row group
+    int pad;
+    long long part;      // float offset of this tile's slot in the partial area
+};
+
+}  // namespace nurbs

@@ -1,0 +1,91 @@
+"""Host-side checks of the C-ABI library (no GPU needed): it builds, loads, exports
+every entry point include/nurbs.h declares, and its planner validates
+descriptors and sizes the workspace without touching the device."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2104_14547_gb300 import _lib, batch, synth
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(__file__)), "include", "nurbs.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(nurbs_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = _lib.load()
+    names = declared_functions()
+    assert len(names) >= 15
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(names) == set(_lib.SIGNATURES)
+
+
+def _plan(kind, descs, cfg=None):
+    lib = _lib.load()
+    h = ctypes.c_void_p()
+    d = np.ascontiguousarray(descs, dtype=batch.DESC_DTYPE)
+    st = lib.nurbs_plan_create(kind, d.ctypes.data_as(ctypes.POINTER(_lib.Desc)), len(d),
+                               ctypes.byref(cfg) if cfg else None, ctypes.byref(h))
+    return st, h
+
+
+def test_planner_tiles_and_points():
+    surfs, _ = synth.bicubic_batch(0, batch=3, net=12, grid=40)
+    pk = batch.pack_surfaces(surfs)
+    st, h = _plan(_lib.KIND_SURFACE, pk.descs)
+    assert st == 0
+    lib = _lib.load()
+    assert lib.nurbs_plan_points(h) == 3 * 40 * 40
+    assert lib.nurbs_plan_tiles(h) >= 3
+    assert lib.nurbs_plan_workspace_size(h) > 256
+    # binding needs a real, aligned workspace: rejected before any CUDA call
+    assert lib.nurbs_plan_bind(h, None, 0, None) == 6
+    assert lib.nurbs_eval_surface(h, None, None, None, None, None) == 1
+    lib.nurbs_plan_destroy(h)
+
+
+def test_planner_rejects_bad_descriptors():
+    s = synth.single_bicubic(0)
+    pk = batch.pack_surfaces([s])
+    d = pk.descs.copy()
+    d["p"] = 0
+    assert _plan(_lib.KIND_SURFACE, d)[0] == 3          # degree
+    d = pk.descs.copy()
+    d["p"] = 6
+    assert _plan(_lib.KIND_SURFACE, d)[0] == 3
+    d = pk.descs.copy()
+    d["n1"] = 3                                          # fewer than p+1 control points
+    assert _plan(_lib.KIND_SURFACE, d)[0] == 3
+    d = pk.descs.copy()
+    d["nu"] = -1
+    assert _plan(_lib.KIND_SURFACE, d)[0] == 1
+    assert _plan(7, pk.descs)[0] == 1                    # kind
+    cfg = _lib.TileCfg(0, 9, 0, 0)                       # more warps than the kernels allow
+    assert _plan(_lib.KIND_SURFACE, pk.descs, cfg)[0] == 1
+
+
+def test_curve_plan_and_empty_items():
+    rng = np.random.default_rng(0)
+    cs = [synth.curve(rng, 3, 20, n) for n in (0, 1, 300, 1025)]
+    pk = batch.pack_curves(cs)
+    st, h = _plan(_lib.KIND_CURVE, pk.descs)
+    assert st == 0
+    lib = _lib.load()
+    assert lib.nurbs_plan_points(h) == 0 + 1 + 300 + 1025
+    # a curve plan refuses the surface entry point
+    assert lib.nurbs_plan_tiles(h) >= 4
+    lib.nurbs_plan_destroy(h)
+
+
+def test_status_strings():
+    lib = _lib.load()
+    for k in range(10):
+        assert lib.nurbs_status_string(k).decode()
