@@ -114,7 +114,6 @@ def make_workload(device):
     surfs, targets = synth.bicubic_batch(0, WORKLOAD["batch"], WORKLOAD["net"], WORKLOAD["grid"])
     pk = batch.pack_surfaces(surfs)
     tk = batch.pack_surfaces(targets)
-    plan = batch.Plan.for_packed(pk, device=device)
     kn, ct, pr = batch.to_device(pk, device)
     # the target surface: the forward of an independent control net on the same knots and grid
     tplan = batch.Plan.for_packed(tk, device=device)
@@ -122,7 +121,7 @@ def make_workload(device):
     target = torch.empty((pk.npts, 3), device=device)
     tplan.eval(kn, tct, pr, target)
     torch.cuda.synchronize(device)
-    return pk, plan, kn, ct, pr, target
+    return pk, kn, ct, pr, target
 
 
 def run_ours(args):
@@ -136,14 +135,18 @@ def run_ours(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    from paper_2104_14547_gb300 import batch
+    from paper_2104_14547_gb300 import batch, tune
 
-    pk, plan, kn, ct, pr, target = make_workload(dev)
+    pk, kn, ct, pr, target = make_workload(dev)
     npts = pk.npts
     pts = torch.empty((npts, 3), device=dev)
     gc = torch.empty_like(ct)
     gk = torch.empty_like(kn)
     loss = torch.empty(pk.count, device=dev)
+    # tile shape from the autotuner (untimed), then the plan the step runs
+    best, table = tune.autotune(pk, dict(knots=kn, ctrl=ct, params=pr, target=target, pts=pts, grad_ctrl=gc,
+                                         grad_knots=gk, loss=loss), op="mse", device=dev)
+    plan = batch.Plan.for_packed(pk, device=dev, warps=best[0], rows=best[1])
     scale = 2.0 / (3.0 * npts)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)   # > L2 (129 MB)
     stream = torch.cuda.current_stream(dev)
@@ -246,7 +249,8 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded, shapes of the paper's fitting workloads)",
             "config": dict(WORKLOAD, l2_flush="256 MiB write before every timed step", parallelism=f"replicas{world}",
-                           points_per_step=npts * world),
+                           points_per_step=npts * world, tile={"warps": best[0], "rows": best[1]},
+                           autotune_ms={f"w{w}r{r}": round(v, 4) for (w, r), v in table.items()}),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "algorithmic_bytes": abytes,
                          "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy)" if peaks else "fallback 6.8 TB/s",

@@ -42,7 +42,8 @@ struct nurbs_plan {
     int64_t points;
     // shared memory carve-up
     int R, C, acc_cap;
-    int off_misc, off_su, off_u, off_nu, off_sv, off_v, off_nv, off_stage, off_beta, off_duc, off_dvc, off_acc;
+    int off_misc, off_su, off_u, off_nu, off_sv, off_v, off_nv, off_stage, off_beta, off_duc, off_dvc, off_ring,
+        off_jb, off_acc;
     int smem_bytes;
     // workspace layout (bytes)
     size_t items_off, tiles_off, counts_off, part_off, ws_bytes;
@@ -145,13 +146,12 @@ nurbs_status nurbs_plan_create(int32_t kind, const nurbs_desc* h_desc, int32_t c
             int R = it.curve ? 1 : (rows_cfg > 0 ? rows_cfg : 16 * nwr);
             nwr = std::min(nwr, R);
             const int nrt = std::max(1, (it.nu + R - 1) / R);
-            const int rpg_full = (R + nwr - 1) / nwr;
-            it.rcap = std::min(it.n1, rpg_full * (it.p + 1));
+            it.rcap = it.n1;
             it.ku_cap = it.curve ? 0 : it.n1 + it.p + 1;
             it.kv_cap = it.m1 + it.q + 1;
             it.wbase = align4(12 + it.ku_cap + it.kv_cap);
-            it.abase = align4(4 + it.rcap);
-            it.warp_slot = it.abase + 4 * it.rcap * it.m1;
+            it.abase = 8;
+            it.unit_slot = it.abase + 4 * it.rcap * it.m1;
             int ntl = 0;
             for (int rt = 0; rt < nrt; ++rt) {
                 for (int ct = 0; ct < nct; ++ct) {
@@ -167,7 +167,7 @@ nurbs_status nurbs_plan_create(int32_t kind, const nurbs_desc* h_desc, int32_t c
                     tl.nwr = nwr;
                     tl.rpg = std::max(1, (tl.nrows + nwr - 1) / nwr);
                     tl.part = part_floats;
-                    part_floats += it.wbase + (long long)nwc * nwr * it.warp_slot;
+                    part_floats += it.wbase + (long long)nwr * it.unit_slot;
                     part_floats = (part_floats + 63) / 64 * 64;   // 256-byte aligned slots
                     pl->tiles.push_back(tl);
                     maxR = std::max(maxR, tl.nrows);
@@ -191,14 +191,16 @@ nurbs_status nurbs_plan_create(int32_t kind, const nurbs_desc* h_desc, int32_t c
     pl->off_sv = take(4 * maxC);
     pl->off_v = take(4 * maxC);
     pl->off_nv = take(4 * maxC * kMaxBasis);
-    pl->off_stage = take(16 * 32 * NW);
+    pl->off_stage = take(16 * kBatch * 32 * NW);
     pl->off_beta = take(4 * NW * maxR * kMaxBasis);
     pl->off_duc = take(4 * maxR * kMaxKnotWin);
-    pl->off_dvc = take(4 * NW * 32 * kMaxKnotWin);
+    pl->off_dvc = take(4 * NW * maxC * kMaxKnotWin);
+    pl->off_ring = take(4 * NW * kRing * 96);
+    pl->off_jb = take(8 * kJbCap);
     pl->off_acc = pl->off_su;     // the final reduction reuses the tile tables
-    const size_t min_acc = 16 * (size_t)std::max(1024, max_m1);
+    const size_t min_acc = 16 * 1024;
     if (off < (size_t)pl->off_acc + min_acc) off = pl->off_acc + min_acc;
-    pl->acc_cap = (int)((off - pl->off_acc) / 16);
+    pl->acc_cap = (int)(off - pl->off_acc);
     pl->smem_bytes = (int)off;
     // workspace layout
     size_t w = kHeaderBytes;
@@ -283,7 +285,8 @@ nurbs_status launch(const nurbs_plan* cpl, int v, KParams& kp, cudaStream_t s)
     kp.R = pl->R; kp.C = pl->C;
     kp.off_misc = pl->off_misc; kp.off_su = pl->off_su; kp.off_u = pl->off_u; kp.off_nu = pl->off_nu;
     kp.off_sv = pl->off_sv; kp.off_v = pl->off_v; kp.off_nv = pl->off_nv; kp.off_stage = pl->off_stage;
-    kp.off_beta = pl->off_beta; kp.off_duc = pl->off_duc; kp.off_dvc = pl->off_dvc; kp.off_acc = pl->off_acc;
+    kp.off_beta = pl->off_beta; kp.off_duc = pl->off_duc; kp.off_dvc = pl->off_dvc; kp.off_ring = pl->off_ring; kp.off_jb = pl->off_jb;
+    kp.off_acc = pl->off_acc;
     kp.acc_cap = pl->acc_cap;
     const int block = 32 * pl->warps;
     for (PlanGroup& grp : pl->groups) {

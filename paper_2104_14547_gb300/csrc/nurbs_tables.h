@@ -11,10 +11,10 @@
 //   [0..7]    int: ku_lo, nku, kv_lo, nkv, valid, -, -, -
 //   [8]       float: loss (sum of squared differences over the tile)
 //   [12..)    dU partial (ku_cap floats), then dV partial (kv_cap floats)
-//   wbase     warp slots, one per warp of the CTA (ItemDev::warp_slot floats each):
-//               [0..3] int: rows stored, jlo, CW, valid
-//               [4..)  int: the control-row index of each stored row
-//               abase  float4 A[rows stored][m1]: homogeneous adjoint partial
+//   wbase     unit slots, one per row group of the tile (ItemDev::unit_slot floats each):
+//               [0..7] int: ilo, rows, jlo, CW, valid
+//               abase  float4 A[rows][m1]: homogeneous adjoint partial for control
+//                      rows ilo .. ilo+rows-1 and columns jlo .. jlo+CW-1
 #pragma once
 #include <stdint.h>
 
@@ -34,11 +34,11 @@ struct WsHeader {
 struct ItemDev {
     int p, q, n1, m1, nu, nv;
     int first_tile, ntiles;
-    int rcap;        // capacity of stored control rows per warp slot
+    int rcap;        // control rows a unit slot can hold (n1)
     int ku_cap, kv_cap;
-    int wbase;       // float offset of the first warp slot inside a tile slot
-    int warp_slot;   // floats per warp slot
-    int abase;       // float offset of A inside a warp slot (16-byte aligned)
+    int wbase;       // float offset of the first unit slot inside a tile slot
+    int unit_slot;   // floats per unit slot
+    int abase;       // float offset of A inside a unit slot (16-byte aligned)
     int curve;       // 1: a curve item mapped onto the v direction (p == 0, n1 == 1)
     int pad;
     long long knot_u, knot_v, ctrl, param_u, param_v, pts;

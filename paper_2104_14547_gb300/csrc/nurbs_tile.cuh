@@ -3,25 +3,27 @@
 // Work decomposition.  A surface item is cut into tiles of consecutive sample
 // rows (u) and up to 32*warps sample columns (v).  A curve item is mapped onto
 // the v direction (degree-0 u direction with a single row), so one code path
-// serves both.  Inside a tile each warp owns 32 consecutive columns and one row
-// group; lane b keeps its column's span and v-basis in registers and walks the
-// rows of its group in order.  Because the samples are non-decreasing, the
-// u-span is non-decreasing along that walk, so the lane holds a sliding window
-// of P+1 v-contracted homogeneous control rows
+// serves both.  The warps of a tile form `nwr` units (row groups) of `nwc`
+// column warps; lane b of a warp keeps its column's span and v-basis in
+// registers and walks the rows of its unit in order.  Because the samples are
+// non-decreasing, the u-span never decreases along that walk, so the lane holds
+// a sliding window of P+1 v-contracted homogeneous control rows
 //     Qw[r](b) = sum_h Nv_h(b) Pw[s_u - P + r][s_v(b) - Q + h]
 // and each point costs (P+1) 4-wide FMAs (the separable form of Eq. 3).
 //
 // Backward (Eq. 7, Eq. 8, Eq. 9, knot derivative of Sec. 3.2, Alg. 2) with the
 // homogeneous adjoint lambda = (g / W, -S.g / W):
-//   tau[r](b)   = sum_a Nu_r(a) lambda_ab      (same sliding window, registers)
-//   A[i][j]     = sum_b Nv_{j-s_v(b)+Q}(b) tau[i](b)   (v-contraction when row i
-//                 leaves the window; staged through shared memory per warp)
-//   beta_r(a)   = sum_b Qw[r](b) . lambda_ab    (warp shuffle reduction)
+//   tau[r](b)   = sum_a Nu_r(a) lambda_ab         (same sliding window, registers)
+//   A[i][j]     = sum_b Nv_{j-s_v(b)+Q}(b) tau[i](b)
+//                 (rows leaving the window are staged in shared memory, KB at a
+//                  time, and contracted over all tile columns by the whole unit in
+//                  a fixed order: a segmented reduction with no atomics)
+//   beta_r(a)   = sum_b Qw[r](b) . lambda_ab       (warp shuffle reduction)
 //   Gamma_h(b)  = sum_i tau[i](b) . Pw[i][s_v(b)-Q+h]
 // dL/dU and dL/dV follow from beta and Gamma by the reverse-mode knot derivative
-// of the basis.  Every sum is taken in a fixed order: per-warp partials go to the
-// workspace and the last CTA to finish an item adds them tile by tile, warp by
-// warp, so results do not depend on scheduling.
+// of the basis.  Unit partials go to the workspace; the last CTA to finish a
+// tile of an item adds them in unit order, so every result is independent of
+// scheduling (bit-identical run to run, alone or in any batch).
 #pragma once
 #include "nurbs_basis.cuh"
 #include "nurbs_tables.h"
@@ -36,6 +38,9 @@ enum : unsigned {
 
 constexpr int kMaxBasis = 6;    // (max degree + 1)
 constexpr int kMaxKnotWin = 10; // 2 * max degree
+constexpr int kRing = 8;        // rows of dL/dS (or target) in flight per warp
+constexpr int kBatch = 8;       // retired control rows contracted together
+constexpr int kJbCap = 256;     // column ranges cached per tile
 
 struct KParams {
     const ItemDev* items;
@@ -61,8 +66,9 @@ struct KParams {
     int fit;
     // shared-memory carve-up in bytes (host-computed for the plan's largest tile)
     int R, C;
-    int off_misc, off_su, off_u, off_nu, off_sv, off_v, off_nv, off_stage, off_beta, off_duc, off_dvc, off_acc;
-    int acc_cap;             // float4 entries available to the final reduction
+    int off_misc, off_su, off_u, off_nu, off_sv, off_v, off_nv, off_stage, off_beta, off_duc, off_dvc, off_ring,
+        off_jb, off_acc;
+    int acc_cap;             // bytes available to the final reduction from off_acc
 };
 
 __device__ __forceinline__ float4 f4zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
@@ -82,6 +88,26 @@ __device__ __forceinline__ float4 homog(float4 c)
 {
     return make_float4(c.x * c.w, c.y * c.w, c.z * c.w, c.w);
 }
+
+// Barrier over the `nthreads` threads (a multiple of 32) of one unit.
+__device__ __forceinline__ void unit_barrier(int id, int nthreads)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+__device__ __forceinline__ void cp_async4(float* smem_dst, const float* gmem_src)
+{
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async16(float* smem_dst, const float* gmem_src)
+{
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 // Sum of V values across the warp with a halving transpose: after the call,
 // v[0] in lane l holds the full sum of value index `reduce_index<V>(l)`.
@@ -150,7 +176,6 @@ static __device__ __noinline__ void final_reduce(const KParams& kp, int item)
         kp.loss_items[item] = L;
     }
     if (kp.grad_knots != nullptr) {
-        // u knots (surfaces only)
         if (!it.curve) {
             const int nU = it.n1 + it.p + 1;
             for (int K = tid; K < nU; K += bs) {
@@ -180,61 +205,68 @@ static __device__ __noinline__ void final_reduce(const KParams& kp, int item)
     }
     if (kp.grad_ctrl == nullptr && !kp.fit) return;
 
-    float4* acc = reinterpret_cast<float4*>(smem + kp.off_acc);
-    const int m1 = it.m1;
-    const int ch = max(1, kp.acc_cap / m1);
-    for (int i0 = 0; i0 < it.n1; i0 += ch) {
-        const int nr = min(ch, it.n1 - i0);
-        for (int e = tid; e < nr * m1; e += bs) acc[e] = f4zero();
-        __syncthreads();
+    // Stage every unit's header in shared memory (units in tile order, then row-group order).
+    int* s_units = reinterpret_cast<int*>(smem + kp.off_acc);
+    int nunits = 0;
+    for (int t = 0; t < it.ntiles; ++t) nunits += T[t].nwr;
+    const bool staged = nunits * 8 * 4 <= kp.acc_cap;
+    if (staged) {
+        int u0 = 0;
         for (int t = 0; t < it.ntiles; ++t) {
-            const TileDev tl = T[t];
-            const float* sl = tile_slot(kp, tl);
-            const int nws = tl.nwc * tl.nwr;
-            for (int w = 0; w < nws; ++w) {
-                const float* ws = sl + it.wbase + (long long)w * it.warp_slot;
-                const int* wi = reinterpret_cast<const int*>(ws);
-                const int nst = __ldcg(wi + 0), jlo = __ldcg(wi + 1), cw = __ldcg(wi + 2), valid = __ldcg(wi + 3);
-                if (valid && nst > 0) {
-                    const float4* A = reinterpret_cast<const float4*>(ws + it.abase);
-                    for (int e = tid; e < nst * cw; e += bs) {
-                        const int k = e / cw, jj = e - k * cw;
-                        const int i = __ldcg(wi + 4 + k);
-                        if (i >= i0 && i < i0 + nr) {
-                            float4 a = __ldcg(A + (long long)k * m1 + jj);
-                            float4& d = acc[(i - i0) * m1 + jlo + jj];
-                            d.x += a.x; d.y += a.y; d.z += a.z; d.w += a.w;
-                        }
-                    }
+            const float* sl = tile_slot(kp, T[t]);
+            const int nwr = T[t].nwr;
+            for (int e = tid; e < nwr * 5; e += bs) {
+                const int u = e / 5, k = e - u * 5;
+                s_units[(u0 + u) * 8 + k] = __ldcg(reinterpret_cast<const int*>(sl + it.wbase + (long long)u * it.unit_slot) + k);
+            }
+            if (tid < nwr) s_units[(u0 + tid) * 8 + 5] = t;
+            u0 += nwr;
+        }
+    }
+    __syncthreads();
+    const int m1 = it.m1;
+    for (int e = tid; e < it.n1 * m1; e += bs) {
+        const int i = e / m1, j = e - i * m1;
+        float4 a = f4zero();
+        int u = 0;
+        for (int t = 0; t < it.ntiles; ++t) {
+            const float* sl = tile_slot(kp, T[t]);
+            for (int w = 0; w < T[t].nwr; ++w, ++u) {
+                const float* us = sl + it.wbase + (long long)w * it.unit_slot;
+                int ilo, nr, jlo, cw, valid;
+                if (staged) {
+                    const int* h = s_units + u * 8;
+                    ilo = h[0]; nr = h[1]; jlo = h[2]; cw = h[3]; valid = h[4];
+                } else {
+                    const int* h = reinterpret_cast<const int*>(us);
+                    ilo = __ldcg(h + 0); nr = __ldcg(h + 1); jlo = __ldcg(h + 2); cw = __ldcg(h + 3); valid = __ldcg(h + 4);
                 }
-                __syncthreads();
+                if (!valid || i < ilo || i >= ilo + nr || j < jlo || j >= jlo + cw) continue;
+                const float4 v = __ldcg(reinterpret_cast<const float4*>(us + it.abase) + (long long)(i - ilo) * m1 + (j - jlo));
+                a.x += v.x; a.y += v.y; a.z += v.z; a.w += v.w;
             }
         }
-        for (int e = tid; e < nr * m1; e += bs) {
-            const long long idx = it.ctrl + (long long)(i0 + e / m1) * m1 + (e % m1);
-            const float4 c = kp.ctrl[idx];
-            const float4 a = acc[e];
-            // Pw = (w x, w y, w z, w): dL/dx = w A.x, ..., dL/dw = x A.x + y A.y + z A.z + A.w
-            float4 g = make_float4(c.w * a.x, c.w * a.y, c.w * a.z, fmaf(c.x, a.x, fmaf(c.y, a.y, fmaf(c.z, a.z, a.w))));
-            if (kp.grad_ctrl != nullptr) kp.grad_ctrl[idx] = g;
-            if (kp.fit) {
-                float4 mm = kp.adam_m[idx], vv = kp.adam_v[idx];
-                const float ob1 = 1.f - kp.b1, ob2 = 1.f - kp.b2;
-                mm.x = fmaf(kp.b1, mm.x, ob1 * g.x); vv.x = fmaf(kp.b2, vv.x, ob2 * g.x * g.x);
-                mm.y = fmaf(kp.b1, mm.y, ob1 * g.y); vv.y = fmaf(kp.b2, vv.y, ob2 * g.y * g.y);
-                mm.z = fmaf(kp.b1, mm.z, ob1 * g.z); vv.z = fmaf(kp.b2, vv.z, ob2 * g.z * g.z);
-                mm.w = fmaf(kp.b1, mm.w, ob1 * g.w); vv.w = fmaf(kp.b2, vv.w, ob2 * g.w * g.w);
-                float4 cn;
-                cn.x = c.x - kp.lr_t * mm.x / fmaf(sqrtf(vv.x), kp.inv_sqrt_bc2, kp.eps);
-                cn.y = c.y - kp.lr_t * mm.y / fmaf(sqrtf(vv.y), kp.inv_sqrt_bc2, kp.eps);
-                cn.z = c.z - kp.lr_t * mm.z / fmaf(sqrtf(vv.z), kp.inv_sqrt_bc2, kp.eps);
-                cn.w = c.w - kp.lr_t * mm.w / fmaf(sqrtf(vv.w), kp.inv_sqrt_bc2, kp.eps);
-                kp.adam_m[idx] = mm;
-                kp.adam_v[idx] = vv;
-                kp.ctrl_w[idx] = cn;
-            }
+        const long long idx = it.ctrl + e;
+        const float4 c = kp.ctrl[idx];
+        // Pw = (w x, w y, w z, w): dL/dx = w A.x, ..., dL/dw = x A.x + y A.y + z A.z + A.w
+        const float4 g = make_float4(c.w * a.x, c.w * a.y, c.w * a.z, fmaf(c.x, a.x, fmaf(c.y, a.y, fmaf(c.z, a.z, a.w))));
+        if (kp.grad_ctrl != nullptr) kp.grad_ctrl[idx] = g;
+        if (kp.fit) {
+            float4 mm = kp.adam_m[idx], vv = kp.adam_v[idx];
+            const float ob1 = 1.f - kp.b1, ob2 = 1.f - kp.b2;
+            mm.x = fmaf(kp.b1, mm.x, ob1 * g.x); vv.x = fmaf(kp.b2, vv.x, ob2 * g.x * g.x);
+            mm.y = fmaf(kp.b1, mm.y, ob1 * g.y); vv.y = fmaf(kp.b2, vv.y, ob2 * g.y * g.y);
+            mm.z = fmaf(kp.b1, mm.z, ob1 * g.z); vv.z = fmaf(kp.b2, vv.z, ob2 * g.z * g.z);
+            mm.w = fmaf(kp.b1, mm.w, ob1 * g.w); vv.w = fmaf(kp.b2, vv.w, ob2 * g.w * g.w);
+            float4 cn;
+            cn.x = c.x - kp.lr_t * mm.x / fmaf(sqrtf(vv.x), kp.inv_sqrt_bc2, kp.eps);
+            cn.y = c.y - kp.lr_t * mm.y / fmaf(sqrtf(vv.y), kp.inv_sqrt_bc2, kp.eps);
+            cn.z = c.z - kp.lr_t * mm.z / fmaf(sqrtf(vv.z), kp.inv_sqrt_bc2, kp.eps);
+            cn.w = c.w - kp.lr_t * mm.w / fmaf(sqrtf(vv.w), kp.inv_sqrt_bc2, kp.eps);
+            kp.adam_m[idx] = mm;
+            kp.adam_v[idx] = vv;
+            kp.ctrl_w[idx] = cn;
         }
-        __syncthreads();
     }
 }
 
@@ -254,7 +286,7 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
     const ItemDev it = kp.items[tl.item];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, bs = blockDim.x;
 
-    int* s_flag = reinterpret_cast<int*>(smem + kp.off_misc);     // [0] bad, [1] last
+    int* s_flag = reinterpret_cast<int*>(smem + kp.off_misc);          // [0] bad, [1] last
     float* s_red = reinterpret_cast<float*>(smem + kp.off_misc) + 16;  // per-warp loss
     int* s_su = reinterpret_cast<int*>(smem + kp.off_su);
     float* s_u = reinterpret_cast<float*>(smem + kp.off_u);
@@ -339,31 +371,43 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
     const int wc = warp % nwc, wr = warp / nwc;
     const int ra = wr * rpg, rb = min(nrows, ra + rpg);
     const int wcol0 = wc * 32;
-    const int nvw = min(32, ncols - wcol0);            // valid columns of this warp
-    const bool wactive = !bad && wr < nwr && ra < rb && nvw > 0;
+    const int nvw = max(0, min(32, ncols - wcol0));     // valid columns of this warp
+    const bool uactive = !bad && wr < nwr && ra < rb;   // the warp's unit has work
+    const int uthreads = nwc * 32, ut = wc * 32 + lane; // threads of the unit, index in it
     const int bl = wcol0 + lane;
-    const bool cvalid = wactive && lane < nvw;
+    const bool cvalid = uactive && lane < nvw;
     const int blc = min(bl, ncols - 1);
 
     float* slot = GRAD ? tile_slot(kp, tl) : nullptr;
-    float* wslot = GRAD ? slot + it.wbase + (long long)warp * it.warp_slot : nullptr;
+    float* uslot = GRAD ? slot + it.wbase + (long long)wr * it.unit_slot : nullptr;
 
     float lossacc = 0.f;
     float Gam[QB];
 #pragma unroll
     for (int h = 0; h < QB; ++h) Gam[h] = 0.f;
 
-    if (wactive) {
+    // per-tile table of the sample-column range [lo, hi) feeding each control column
+    // jlo_t + jj of the A contraction (all units of a tile span the same columns)
+    const int jlo_t = bad ? 0 : s_sv[0] - Q;
+    const int cw_t = bad ? 0 : s_sv[ncols - 1] - jlo_t + 1;
+    int2* s_jb = reinterpret_cast<int2*>(smem + kp.off_jb);
+    if constexpr (GRAD) {
+        for (int jj = tid; jj < min(cw_t, kJbCap); jj += bs)
+            s_jb[jj] = make_int2(lower_bound_i(s_sv, ncols, jlo_t + jj), lower_bound_i(s_sv, ncols, jlo_t + jj + Q + 1));
+        __syncthreads();
+    }
+
+    if (uactive) {
         const int svb = s_sv[blc];
         const float vb = s_v[blc];
         float Nv[QB];
 #pragma unroll
         for (int h = 0; h < QB; ++h) Nv[h] = s_nv[blc * kMaxBasis + h];
         const float4* __restrict__ cbase = kp.ctrl + it.ctrl + (svb - Q);  // column of h = 0
-        const long long m1 = it.m1;
+        const int m1 = it.m1;
 
         auto computeQ = [&](int i) -> float4 {
-            const float4* cr = cbase + (long long)i * m1;
+            const float4* cr = cbase + i * m1;
             float4 acc = f4zero();
 #pragma unroll
             for (int h = 0; h < QB; ++h) {
@@ -377,52 +421,70 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
             return acc;
         };
 
-        // warp's v-knot column range and, for lane-as-column jj = lane, its sample range
-        const int jlo_w = s_sv[wcol0] - Q;
-        const int cw_w = s_sv[wcol0 + nvw - 1] - jlo_w + 1;
-        int bj_lo = 0, bj_hi = 0;
-        if (GRAD && lane < cw_w) {
-            const int j = jlo_w + lane;
-            bj_lo = lower_bound_i(s_sv + wcol0, nvw, j);
-            bj_hi = lower_bound_i(s_sv + wcol0, nvw, j + Q + 1);
-        }
-        float4* stage = reinterpret_cast<float4*>(smem + kp.off_stage) + warp * 32;
-        int nst = 0;
-        int* wil = GRAD ? reinterpret_cast<int*>(wslot) + 4 : nullptr;
-        float4* wA = GRAD ? reinterpret_cast<float4*>(wslot + it.abase) : nullptr;
-
-        // Row i of the window is complete for this warp: fold it into A (and Gamma).
+        // Retired control rows (consecutive, from ilo) wait in tbuf until kBatch of
+        // them are contracted together over the tile columns by the whole unit.
+        float4* tbuf = reinterpret_cast<float4*>(smem + kp.off_stage) + wr * (kBatch * uthreads);
+        float4* uA = GRAD ? reinterpret_cast<float4*>(uslot + it.abase) : nullptr;
+        int nb = 0, nst = 0, ilo = -1;
+        auto flush = [&]() {
+            unit_barrier(1 + wr, uthreads);
+            const int tasks = nb * cw_t;
+            for (int task = ut; task < tasks; task += uthreads) {
+                const int k = task / cw_t, jj = task - k * cw_t;
+                const int j = jlo_t + jj;
+                int lo, hi;
+                if (jj < kJbCap) { const int2 r2 = s_jb[jj]; lo = r2.x; hi = r2.y; }
+                else { lo = lower_bound_i(s_sv, ncols, j); hi = lower_bound_i(s_sv, ncols, j + Q + 1); }
+                const float4* tb = tbuf + k * uthreads;
+                float4 acc = f4zero();
+                for (int b = lo; b < hi; ++b) acc = fma4(s_nv[b * kMaxBasis + (j - s_sv[b] + Q)], tb[b], acc);
+                uA[(nst + k) * m1 + jj] = acc;
+            }
+            nst += nb;
+            nb = 0;
+            unit_barrier(1 + wr, uthreads);
+        };
+        // Row i of the window is complete for this unit (rows retire in increasing,
+        // consecutive order; rows skipped by a jump retire with tau = 0).
         auto retire = [&](int i, float4 tv) {
             if constexpr (KNOTS) {
-                const float4* cr = cbase + (long long)i * m1;
+                const float4* cr = cbase + i * m1;
 #pragma unroll
                 for (int h = 0; h < QB; ++h) Gam[h] += dot4(tv, homog(__ldg(cr + h)));
             }
-            stage[lane] = tv;
-            __syncwarp();
-            for (int jj = lane; jj < cw_w; jj += 32) {
-                const int j = jlo_w + jj;
-                int lo = bj_lo, hi = bj_hi;
-                if (jj >= 32) {
-                    lo = lower_bound_i(s_sv + wcol0, nvw, j);
-                    hi = lower_bound_i(s_sv + wcol0, nvw, j + Q + 1);
-                }
-                float4 acc = f4zero();
-                for (int b = lo; b < hi; ++b) {
-                    const int h = j - s_sv[wcol0 + b] + Q;
-                    acc = fma4(s_nv[(wcol0 + b) * kMaxBasis + h], stage[b], acc);
-                }
-                wA[(long long)nst * m1 + jj] = acc;
-            }
-            if (lane == 0) wil[nst] = i;
-            ++nst;
-            __syncwarp();
+            if (ilo < 0) ilo = i;
+            tbuf[nb * uthreads + ut] = tv;
+            if (++nb == kBatch) flush();
         };
+
+        // ring of incoming dL/dS (or target) rows for this warp's columns
+        float* ring = reinterpret_cast<float*>(smem + kp.off_ring) + warp * (kRing * 96);
+        const int nf = 3 * nvw;
+        const long long prow0 = it.pts + (long long)tl.row0 * it.nv + tl.col0 + wcol0;  // point index of (ra = 0, lane 0)
+        const float* grow0 = GRAD ? kp.gin + 3 * prow0 : nullptr;
+        const bool al16 = ((prow0 & 3) == 0) && ((it.nv & 3) == 0) && ((nvw & 3) == 0);
+        auto issue = [&](int r) {
+            if (r < rb && nf > 0) {
+                float* dst = ring + ((r - ra) & (kRing - 1)) * 96;
+                const float* src = grow0 + 3LL * r * it.nv;
+                if (al16) {
+                    if (lane * 4 < nf) cp_async16(dst + lane * 4, src + lane * 4);
+                } else {
+                    for (int k = lane; k < nf; k += 32) cp_async4(dst + k, src + k);
+                }
+            }
+            cp_async_commit();
+        };
+        if constexpr (GRAD) {
+#pragma unroll
+            for (int d = 0; d < kRing - 1; ++d) issue(ra + d);
+        }
 
         float4 Qw[PB];
         float4 tau[PB];
         int cur = -1;
         for (int r = ra; r < rb; ++r) {
+            if constexpr (GRAD) issue(r + kRing - 1);
             const int s = s_su[r];
             float Nu[PB];
 #pragma unroll
@@ -433,6 +495,7 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
                         if (cur >= 0) {
 #pragma unroll
                             for (int k = 0; k < PB; ++k) retire(cur - P + k, tau[k]);
+                            for (int i = cur + 1; i < s - P; ++i) retire(i, f4zero());
                         }
                     }
 #pragma unroll
@@ -453,30 +516,32 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
             float4 Sw = f4zero();
 #pragma unroll
             for (int k = 0; k < PB; ++k) Sw = fma4(Nu[k], Qw[k], Sw);
-            const float inv = 1.f / Sw.w;
+            const float inv = __fdividef(1.f, Sw.w);
             const float Sx = Sw.x * inv, Sy = Sw.y * inv, Sz = Sw.z * inv;
-            const long long pidx = it.pts + (long long)(tl.row0 + r) * it.nv + (tl.col0 + bl);
             if constexpr (!GRAD) {
                 if (cvalid) {
-                    float* o = kp.pts + 3 * pidx;
-                    o[0] = Sx; o[1] = Sy; o[2] = Sz;
+                    float* oo = kp.pts + 3 * (prow0 + lane + (long long)r * it.nv);
+                    oo[0] = Sx; oo[1] = Sy; oo[2] = Sz;
                 }
             } else {
+                cp_async_wait<kRing - 1>();
+                __syncwarp();
+                const float* gp = ring + ((r - ra) & (kRing - 1)) * 96 + 3 * lane;
                 float gx = 0.f, gy = 0.f, gz = 0.f;
                 if (cvalid) {
-                    const float* gp = kp.gin + 3 * pidx;
                     if (kp.gsrc == 0) {
-                        gx = __ldg(gp + 0); gy = __ldg(gp + 1); gz = __ldg(gp + 2);
+                        gx = gp[0]; gy = gp[1]; gz = gp[2];
                     } else {
-                        const float dx = Sx - __ldg(gp + 0), dy = Sy - __ldg(gp + 1), dz = Sz - __ldg(gp + 2);
+                        const float dx = Sx - gp[0], dy = Sy - gp[1], dz = Sz - gp[2];
                         lossacc = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, lossacc)));
                         gx = kp.grad_scale * dx; gy = kp.grad_scale * dy; gz = kp.grad_scale * dz;
                     }
                     if (kp.pts != nullptr) {
-                        float* o = kp.pts + 3 * pidx;
-                        o[0] = Sx; o[1] = Sy; o[2] = Sz;
+                        float* oo = kp.pts + 3 * (prow0 + lane + (long long)r * it.nv);
+                        oo[0] = Sx; oo[1] = Sy; oo[2] = Sz;
                     }
                 }
+                __syncwarp();   // the slot is refilled by the next iteration's issue
                 // lambda = dL/dS' for S' = (NR, W): (g / W, -S.g / W)
                 const float gbx = gx * inv, gby = gy * inv, gbz = gz * inv;
                 const float4 lam = make_float4(gbx, gby, gbz, -fmaf(Sx, gbx, fmaf(Sy, gby, Sz * gbz)));
@@ -495,25 +560,27 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
             }
         }
         if constexpr (GRAD) {
+            cp_async_wait<0>();
 #pragma unroll
             for (int k = 0; k < PB; ++k) retire(cur - P + k, tau[k]);
-            if (lane == 0) {
-                int* wh = reinterpret_cast<int*>(wslot);
-                wh[0] = nst; wh[1] = jlo_w; wh[2] = cw_w; wh[3] = 1;
+            if (nb > 0) flush();
+            if (ut == 0) {
+                int* uh = reinterpret_cast<int*>(uslot);
+                uh[0] = ilo; uh[1] = nst; uh[2] = jlo_t; uh[3] = cw_t; uh[4] = 1;
             }
             if constexpr (KNOTS) {
                 if (cvalid) {
                     float dk[2 * Q + 1];
                     basis_knot_vjp<Q>(svb, vb, V, Gam, dk);
-                    float* dv = reinterpret_cast<float*>(smem + kp.off_dvc) + ((wr * nwc * 32) + bl) * kMaxKnotWin;
+                    float* dv = reinterpret_cast<float*>(smem + kp.off_dvc) + (wr * kp.C + bl) * kMaxKnotWin;
 #pragma unroll
                     for (int k = 0; k < 2 * Q; ++k) dv[k] = dk[k];
                 }
             }
         }
-    } else if (GRAD && warp < nwc * nwr && lane == 0) {
-        int* wh = reinterpret_cast<int*>(wslot);
-        wh[0] = 0; wh[1] = 0; wh[2] = 0; wh[3] = 0;
+    } else if (GRAD && wr < nwr && wc == 0 && lane == 0) {
+        int* uh = reinterpret_cast<int*>(uslot);
+        uh[0] = 0; uh[1] = 0; uh[2] = 0; uh[3] = 0; uh[4] = 0;
     }
 
     if constexpr (GRAD) {
@@ -531,7 +598,8 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
         }
         if constexpr (KNOTS) {
             if (!bad) {
-                // dL/dU: per row, beta summed over column warps in order, then the
+                const int nwc_valid = (ncols + 31) / 32;
+                // dL/dU: per row, beta summed over the column warps in order, then the
                 // reverse-mode knot derivative of the row's basis
                 if constexpr (P > 0) {
                     float* s_beta = reinterpret_cast<float*>(smem + kp.off_beta);
@@ -540,7 +608,7 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
                         float bsum[PB];
 #pragma unroll
                         for (int k = 0; k < PB; ++k) bsum[k] = 0.f;
-                        for (int w = 0; w < nwc; ++w)
+                        for (int w = 0; w < nwc_valid; ++w)
 #pragma unroll
                             for (int k = 0; k < PB; ++k) bsum[k] += s_beta[(w * kp.R + r) * kMaxBasis + k];
                         float dk[2 * P + 1];
@@ -580,7 +648,7 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
                         if (g * rpg >= nrows) break;
                         for (int c = clo; c < chi; ++c) {
                             const int o = kk - (s_sv[c] - Q + 1);
-                            acc += s_dvc[((g * nwc * 32) + c) * kMaxKnotWin + o];
+                            acc += s_dvc[(g * kp.C + c) * kMaxKnotWin + o];
                         }
                     }
                     slot[12 + it.ku_cap + K] = acc;
