@@ -6,9 +6,13 @@ namespace nurbs {
 template <int Q>
 static KernelVariant pick(int v)
 {
-    if (v == 0) return VariantOf<3, Q, false, false>::get();
-    if (v == 1) return VariantOf<3, Q, true, false>::get();
-    return VariantOf<3, Q, true, true>::get();
+    switch (v) {
+        case 0: return VariantOf<3, Q, false, false, false>::get();
+        case 1: return VariantOf<3, Q, true, false, false>::get();
+        case 2: return VariantOf<3, Q, true, true, false>::get();
+        case 3: return VariantOf<3, Q, true, false, true>::get();
+        default: return VariantOf<3, Q, true, true, true>::get();
+    }
 }
 
 KernelVariant variant_p3(int v, int q)

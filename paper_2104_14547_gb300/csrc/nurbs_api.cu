@@ -30,7 +30,7 @@ nurbs_status cuda_fail(cudaError_t e)
 struct PlanGroup {
     int p, q;         // internal degrees (p == 0 for curves)
     int t0, t1;       // tile range
-    int grid[3];      // CTAs per launch for forward / backward / backward + knots (0 = unknown)
+    int grid[5];      // CTAs per launch of each kernel variant (0 = unknown)
 };
 
 struct nurbs_plan {
@@ -43,7 +43,7 @@ struct nurbs_plan {
     // shared memory carve-up
     int R, C, acc_cap;
     int off_misc, off_su, off_u, off_nu, off_sv, off_v, off_nv, off_stage, off_beta, off_duc, off_dvc, off_ring,
-        off_jb, off_acc;
+        off_jb, off_win, off_run, off_crun, off_knots, off_w, off_acc;
     int smem_bytes;
     // workspace layout (bytes)
     size_t items_off, tiles_off, counts_off, part_off, ws_bytes;
@@ -133,7 +133,7 @@ nurbs_status nurbs_plan_create(int32_t kind, const nurbs_desc* h_desc, int32_t c
         PlanGroup grp;
         grp.p = gp; grp.q = gq;
         grp.t0 = (int)pl->tiles.size();
-        grp.grid[0] = grp.grid[1] = grp.grid[2] = 0;
+        for (int v = 0; v < 5; ++v) grp.grid[v] = 0;
         for (int32_t k = 0; k < count; ++k) {
             ItemDev& it = pl->items[k];
             if (it.p != gp || it.q != gq) continue;
@@ -180,6 +180,12 @@ nurbs_status nurbs_plan_create(int32_t kind, const nurbs_desc* h_desc, int32_t c
         if (grp.t1 > grp.t0) pl->groups.push_back(grp);
     }
     // shared memory carve-up for the largest tile
+    int max_nwc = 1, max_nwr = 1, max_unit_cols = 32;
+    for (const TileDev& tl : pl->tiles) {
+        max_nwc = std::max(max_nwc, tl.nwc);
+        max_nwr = std::max(max_nwr, tl.nwr);
+        max_unit_cols = std::max(max_unit_cols, tl.nwr * tl.nwc * 32);
+    }
     pl->R = maxR;
     pl->C = maxC;
     size_t off = 0;
@@ -191,14 +197,28 @@ nurbs_status nurbs_plan_create(int32_t kind, const nurbs_desc* h_desc, int32_t c
     pl->off_sv = take(4 * maxC);
     pl->off_v = take(4 * maxC);
     pl->off_nv = take(4 * maxC * kMaxBasis);
-    pl->off_stage = take(16 * kBatch * 32 * NW);
-    pl->off_beta = take(4 * NW * maxR * kMaxBasis);
+    pl->off_stage = take(16 * kBatch * max_unit_cols);
+    pl->off_beta = take(4 * max_nwc * maxR * kMaxBasis);
     pl->off_duc = take(4 * maxR * kMaxKnotWin);
-    pl->off_dvc = take(4 * NW * maxC * kMaxKnotWin);
-    pl->off_ring = take(4 * NW * kRing * 96);
+    pl->off_dvc = take(4 * max_nwr * maxC * kMaxKnotWin);
+    pl->off_ring = take(4 * NW * kRing * 96);   // only the grad kernels use it
     pl->off_jb = take(8 * kJbCap);
+    pl->off_win = take(16 * kWinCap);
+    pl->off_run = take(4 * maxR);
+    pl->off_crun = take(4 * maxC);
+    int max_knots = 4;
+    for (const ItemDev& it : pl->items)
+        max_knots = std::max(max_knots, align4(it.n1 + it.p + 1) + it.m1 + it.q + 1);
+    pl->off_knots = take(4 * max_knots);
+    pl->off_w = take(4 * (kJbCap + maxC * kMaxBasis));
     pl->off_acc = pl->off_su;     // the final reduction reuses the tile tables
-    const size_t min_acc = 16 * 1024;
+    int max_units = 1;
+    for (const ItemDev& it : pl->items) {
+        int u = 0;
+        for (int t = it.first_tile; t < it.first_tile + it.ntiles; ++t) u += pl->tiles[t].nwr;
+        max_units = std::max(max_units, u);
+    }
+    const size_t min_acc = std::max<size_t>(16 * 1024, 32 * (size_t)max_units);
     if (off < (size_t)pl->off_acc + min_acc) off = pl->off_acc + min_acc;
     pl->acc_cap = (int)(off - pl->off_acc);
     pl->smem_bytes = (int)off;
@@ -269,7 +289,8 @@ KernelVariant variant_for(int v, int p, int q)
     }
 }
 
-// Launch variant v (0 forward, 1 backward, 2 backward + knots): one persistent
+// Launch variant v (0 forward, 1/2 backward from dL/dS without/with knots, 3/4 the
+// same from an MSE target): one persistent
 // kernel per degree group, in group order on `s`.
 nurbs_status launch(const nurbs_plan* cpl, int v, KParams& kp, cudaStream_t s)
 {
@@ -285,7 +306,7 @@ nurbs_status launch(const nurbs_plan* cpl, int v, KParams& kp, cudaStream_t s)
     kp.R = pl->R; kp.C = pl->C;
     kp.off_misc = pl->off_misc; kp.off_su = pl->off_su; kp.off_u = pl->off_u; kp.off_nu = pl->off_nu;
     kp.off_sv = pl->off_sv; kp.off_v = pl->off_v; kp.off_nv = pl->off_nv; kp.off_stage = pl->off_stage;
-    kp.off_beta = pl->off_beta; kp.off_duc = pl->off_duc; kp.off_dvc = pl->off_dvc; kp.off_ring = pl->off_ring; kp.off_jb = pl->off_jb;
+    kp.off_beta = pl->off_beta; kp.off_duc = pl->off_duc; kp.off_dvc = pl->off_dvc; kp.off_ring = pl->off_ring; kp.off_jb = pl->off_jb; kp.off_win = pl->off_win; kp.off_run = pl->off_run; kp.off_crun = pl->off_crun; kp.off_knots = pl->off_knots; kp.off_w = pl->off_w;
     kp.off_acc = pl->off_acc;
     kp.acc_cap = pl->acc_cap;
     const int block = 32 * pl->warps;
@@ -328,7 +349,7 @@ int32_t nurbs_plan_ctas(const nurbs_plan* plan)
 {
     if (plan == nullptr) return 0;
     int n = 0;
-    for (const PlanGroup& g : plan->groups) n += std::max(g.grid[0], std::max(g.grid[1], g.grid[2]));
+    for (const PlanGroup& g : plan->groups) n += *std::max_element(g.grid, g.grid + 5);
     return n;
 }
 
@@ -398,7 +419,8 @@ static nurbs_status grad_common(const nurbs_plan* pl, const float* knots, const 
         kp.b2 = hp->beta2;
         kp.eps = hp->eps;
     }
-    return launch(pl, grad_knots != nullptr ? 2 : 1, kp, reinterpret_cast<cudaStream_t>(stream));
+    const int v = (gsrc == 1 ? 3 : 1) + (grad_knots != nullptr ? 1 : 0);
+    return launch(pl, v, kp, reinterpret_cast<cudaStream_t>(stream));
 }
 
 nurbs_status nurbs_backward(const nurbs_plan* plan, const float* knots, const float* ctrl,

@@ -1,20 +1,31 @@
 // Device building blocks shared by the libnurbs kernels: knot-span search,
-// nonzero Cox-de Boor basis and its reverse-mode knot derivative.
+// nonzero Cox-de Boor basis and its reverse-mode knot derivative.  The knot
+// vectors are read through plain pointers (the kernels stage them in shared
+// memory first).
 #pragma once
 #include <cuda_runtime.h>
 
 namespace nurbs {
 
+// Reciprocal with one MUFU op (relative error below 2^-22 for normal inputs);
+// every denominator here is a positive knot difference.
+__device__ __forceinline__ float frcp(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // Knot-span search (Sec. 3.1 step 1): the largest k in [p, n] with U[k] <= u,
 // and n when u >= U[n+1].  Half-open spans, so a zero-length span is never
-// returned.  U is read through the read-only cache.
-__device__ __forceinline__ int find_span(int n, int p, float u, const float* __restrict__ U)
+// returned.
+__device__ __forceinline__ int find_span(int n, int p, float u, const float* U)
 {
-    if (u >= __ldg(U + n + 1)) return n;
+    if (u >= U[n + 1]) return n;
     int lo = p, hi = n;
     while (lo < hi) {
         int mid = (lo + hi + 1) >> 1;
-        if (__ldg(U + mid) <= u) lo = mid; else hi = mid - 1;
+        if (U[mid] <= u) lo = mid; else hi = mid - 1;
     }
     return lo;
 }
@@ -23,19 +34,19 @@ __device__ __forceinline__ int find_span(int n, int p, float u, const float* __r
 // triangular scheme (each level from the previous one; the denominators
 // U_{s+r+1} - U_{s+1-j+r} are positive on a non-empty span).
 template <int P>
-__device__ __forceinline__ void basis_funs(int s, float u, const float* __restrict__ U, float (&N)[P + 1])
+__device__ __forceinline__ void basis_funs(int s, float u, const float* U, float (&N)[P + 1])
 {
     N[0] = 1.f;
     if constexpr (P > 0) {
         float left[P + 1], right[P + 1];
 #pragma unroll
         for (int j = 1; j <= P; ++j) {
-            left[j] = u - __ldg(U + s + 1 - j);
-            right[j] = __ldg(U + s + j) - u;
+            left[j] = u - U[s + 1 - j];
+            right[j] = U[s + j] - u;
             float saved = 0.f;
 #pragma unroll
             for (int r = 0; r < j; ++r) {
-                float temp = N[r] / (right[r + 1] + left[j - r]);
+                float temp = N[r] * frcp(right[r + 1] + left[j - r]);
                 N[r] = fmaf(right[r + 1], temp, saved);
                 saved = left[j - r] * temp;
             }
@@ -50,7 +61,7 @@ __device__ __forceinline__ void basis_funs(int s, float u, const float* __restri
 // Given the cotangent nb[r] = dL/dN_{s-P+r}(u), writes
 //   dk[k] = sum_r nb[r] * dN_{s-P+r}(u) / dU[s-P+1+k],  k = 0 .. 2P-1.
 template <int P>
-__device__ __forceinline__ void basis_knot_vjp(int s, float u, const float* __restrict__ U,
+__device__ __forceinline__ void basis_knot_vjp(int s, float u, const float* U,
                                                const float (&nb_in)[P + 1], float (&dk)[2 * P + 1])
 {
     if constexpr (P == 0) {
@@ -61,12 +72,12 @@ __device__ __forceinline__ void basis_knot_vjp(int s, float u, const float* __re
         tri[0][0] = 1.f;
 #pragma unroll
         for (int j = 1; j <= P; ++j) {
-            left[j] = u - __ldg(U + s + 1 - j);
-            right[j] = __ldg(U + s + j) - u;
+            left[j] = u - U[s + 1 - j];
+            right[j] = U[s + j] - u;
             float saved = 0.f;
 #pragma unroll
             for (int r = 0; r < j; ++r) {
-                float temp = tri[j - 1][r] / (right[r + 1] + left[j - r]);
+                float temp = tri[j - 1][r] * frcp(right[r + 1] + left[j - r]);
                 tri[j][r] = fmaf(right[r + 1], temp, saved);
                 saved = left[j - r] * temp;
             }
@@ -80,14 +91,14 @@ __device__ __forceinline__ void basis_knot_vjp(int s, float u, const float* __re
             float pb[P + 1];
 #pragma unroll
             for (int r = 0; r < j; ++r) {
-                float den = right[r + 1] + left[j - r];
-                float temp = tri[j - 1][r] / den;
+                const float iden = frcp(right[r + 1] + left[j - r]);
+                float temp = tri[j - 1][r] * iden;
                 // temp feeds tri[j][r] (times right[r+1]) and tri[j][r+1] (times left[j-r])
                 float tb = fmaf(right[r + 1], nb[r], left[j - r] * nb[r + 1]);
-                float denb = -tb * temp / den;
+                float denb = -tb * temp * iden;
                 rb[r + 1] += fmaf(temp, nb[r], denb);
                 lb[j - r] += fmaf(temp, nb[r + 1], denb);
-                pb[r] = tb / den;
+                pb[r] = tb * iden;
             }
 #pragma unroll
             for (int r = 0; r < j; ++r) nb[r] = pb[r];

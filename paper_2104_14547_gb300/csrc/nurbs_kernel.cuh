@@ -5,7 +5,7 @@
 
 namespace nurbs {
 
-template <int P, int Q, bool GRAD, bool KNOTS>
+template <int P, int Q, bool GRAD, bool KNOTS, bool MSE>
 __global__ void __launch_bounds__(256, 2) tiles_kernel(const __grid_constant__ KParams kp)
 {
     __shared__ int s_t;
@@ -15,7 +15,7 @@ __global__ void __launch_bounds__(256, 2) tiles_kernel(const __grid_constant__ K
         const int t = s_t;
         __syncthreads();
         if (t >= kp.t1) break;
-        tile_body<P, Q, GRAD, KNOTS>(kp, t);
+        tile_body<P, Q, GRAD, KNOTS, MSE>(kp, t);
     }
     // the last CTA out rearms the queue for the next launch on this workspace
     if (threadIdx.x == 0) {
@@ -36,25 +36,26 @@ struct KernelVariant {
     cudaError_t (*set_smem)(int smem);
 };
 
-template <int P, int Q, bool G, bool K>
+template <int P, int Q, bool G, bool K, bool M>
 struct VariantOf {
     static cudaError_t launch(const KParams& kp, int grid, int block, int smem, cudaStream_t s)
     {
-        tiles_kernel<P, Q, G, K><<<grid, block, smem, s>>>(kp);
+        tiles_kernel<P, Q, G, K, M><<<grid, block, smem, s>>>(kp);
         return cudaGetLastError();
     }
     static cudaError_t occupancy(int* n, int block, int smem)
     {
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, tiles_kernel<P, Q, G, K>, block, smem);
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, tiles_kernel<P, Q, G, K, M>, block, smem);
     }
     static cudaError_t set_smem(int smem)
     {
-        return cudaFuncSetAttribute(tiles_kernel<P, Q, G, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        return cudaFuncSetAttribute(tiles_kernel<P, Q, G, K, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     }
     static KernelVariant get() { return KernelVariant{launch, occupancy, set_smem}; }
 };
 
-// variant: 0 forward, 1 backward, 2 backward with knot gradients.
+// variant: 0 forward; 1 / 2 backward from dL/dS without / with knot gradients;
+// 3 / 4 the same from an MSE target.
 // Defined per u degree in k_p<P>.cu.
 KernelVariant variant_p0(int v, int q);
 KernelVariant variant_p1(int v, int q);

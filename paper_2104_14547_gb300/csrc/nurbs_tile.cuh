@@ -36,11 +36,12 @@ enum : unsigned {
     kErrOrder = 1u << 5,
 };
 
-constexpr int kMaxBasis = 6;    // (max degree + 1)
+constexpr int kMaxBasis = 8;    // basis table stride: (max degree + 1) rounded up to a float4 pair
 constexpr int kMaxKnotWin = 10; // 2 * max degree
-constexpr int kRing = 8;        // rows of dL/dS (or target) in flight per warp
-constexpr int kBatch = 8;       // retired control rows contracted together
+constexpr int kRing = 16;       // rows of dL/dS (or target) in flight per warp (power of two)
+constexpr int kBatch = 4;       // retired control rows contracted together
 constexpr int kJbCap = 256;     // column ranges cached per tile
+constexpr int kWinCap = 1024;   // control points staged in shared memory (whole net, else the tile's window)
 
 struct KParams {
     const ItemDev* items;
@@ -67,7 +68,8 @@ struct KParams {
     // shared-memory carve-up in bytes (host-computed for the plan's largest tile)
     int R, C;
     int off_misc, off_su, off_u, off_nu, off_sv, off_v, off_nv, off_stage, off_beta, off_duc, off_dvc, off_ring,
-        off_jb, off_acc;
+        off_jb, off_win, off_run, off_crun, off_knots, off_w, off_acc;
+
     int acc_cap;             // bytes available to the final reduction from off_acc
 };
 
@@ -88,6 +90,33 @@ __device__ __forceinline__ float4 homog(float4 c)
 {
     return make_float4(c.x * c.w, c.y * c.w, c.z * c.w, c.w);
 }
+
+// Approximate reciprocal (one MUFU op; relative error below 2^-22 for normal inputs).
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// The N basis values of one row / column from its 16-byte aligned table entry.
+template <int N>
+__device__ __forceinline__ void load_basis(const float* p, float (&v)[N])
+{
+    const float4 a = *reinterpret_cast<const float4*>(p);
+    v[0] = a.x;
+    if constexpr (N > 1) v[1] = a.y;
+    if constexpr (N > 2) v[2] = a.z;
+    if constexpr (N > 3) v[3] = a.w;
+    if constexpr (N > 4) {
+        const float4 b = *reinterpret_cast<const float4*>(p + 4);
+        v[4] = b.x;
+        if constexpr (N > 5) v[5] = b.y;
+    }
+}
+
+template <bool B> struct BoolTag { static constexpr bool value = B; };
+template <int N> struct IntTag { static constexpr int value = N; };
 
 // Barrier over the `nthreads` threads (a multiple of 32) of one unit.
 __device__ __forceinline__ void unit_barrier(int id, int nthreads)
@@ -143,7 +172,7 @@ __device__ __forceinline__ int reduce_index(int lane)
     return idx;
 }
 
-template <int N> struct Pow2 { static constexpr int v = N <= 1 ? 1 : N <= 2 ? 2 : N <= 4 ? 4 : 8; };
+template <int N> struct Pow2 { static constexpr int v = N <= 1 ? 1 : N <= 2 ? 2 : N <= 4 ? 4 : N <= 8 ? 8 : N <= 16 ? 16 : 32; };
 
 __device__ __forceinline__ int lower_bound_i(const int* a, int n, int key)
 {
@@ -205,47 +234,31 @@ static __device__ __noinline__ void final_reduce(const KParams& kp, int item)
     }
     if (kp.grad_ctrl == nullptr && !kp.fit) return;
 
-    // Stage every unit's header in shared memory (units in tile order, then row-group order).
+    // Stage every unit's header and partial offset in shared memory (units in
+    // tile order, then row-group order; the planner sizes the buffer).
     int* s_units = reinterpret_cast<int*>(smem + kp.off_acc);
     int nunits = 0;
-    for (int t = 0; t < it.ntiles; ++t) nunits += T[t].nwr;
-    const bool staged = nunits * 8 * 4 <= kp.acc_cap;
-    if (staged) {
+    {
         int u0 = 0;
         for (int t = 0; t < it.ntiles; ++t) {
-            const float* sl = tile_slot(kp, T[t]);
+            const long long base = T[t].part + it.wbase;
             const int nwr = T[t].nwr;
             for (int e = tid; e < nwr * 5; e += bs) {
                 const int u = e / 5, k = e - u * 5;
-                s_units[(u0 + u) * 8 + k] = __ldcg(reinterpret_cast<const int*>(sl + it.wbase + (long long)u * it.unit_slot) + k);
+                s_units[(u0 + u) * 8 + k] = __ldcg(reinterpret_cast<const int*>(kp.part + base + (long long)u * it.unit_slot) + k);
             }
-            if (tid < nwr) s_units[(u0 + tid) * 8 + 5] = t;
+            for (int u = tid; u < nwr; u += bs) {
+                const long long off = base + (long long)u * it.unit_slot + it.abase;
+                s_units[(u0 + u) * 8 + 6] = (int)(off & 0xffffffffLL);
+                s_units[(u0 + u) * 8 + 7] = (int)(off >> 32);
+            }
             u0 += nwr;
         }
+        nunits = u0;
     }
     __syncthreads();
-    const int m1 = it.m1;
-    for (int e = tid; e < it.n1 * m1; e += bs) {
-        const int i = e / m1, j = e - i * m1;
-        float4 a = f4zero();
-        int u = 0;
-        for (int t = 0; t < it.ntiles; ++t) {
-            const float* sl = tile_slot(kp, T[t]);
-            for (int w = 0; w < T[t].nwr; ++w, ++u) {
-                const float* us = sl + it.wbase + (long long)w * it.unit_slot;
-                int ilo, nr, jlo, cw, valid;
-                if (staged) {
-                    const int* h = s_units + u * 8;
-                    ilo = h[0]; nr = h[1]; jlo = h[2]; cw = h[3]; valid = h[4];
-                } else {
-                    const int* h = reinterpret_cast<const int*>(us);
-                    ilo = __ldcg(h + 0); nr = __ldcg(h + 1); jlo = __ldcg(h + 2); cw = __ldcg(h + 3); valid = __ldcg(h + 4);
-                }
-                if (!valid || i < ilo || i >= ilo + nr || j < jlo || j >= jlo + cw) continue;
-                const float4 v = __ldcg(reinterpret_cast<const float4*>(us + it.abase) + (long long)(i - ilo) * m1 + (j - jlo));
-                a.x += v.x; a.y += v.y; a.z += v.z; a.w += v.w;
-            }
-        }
+    const int m1 = it.m1, ncp = it.n1 * m1;
+    auto finish = [&](int e, float4 a) {
         const long long idx = it.ctrl + e;
         const float4 c = kp.ctrl[idx];
         // Pw = (w x, w y, w z, w): dL/dx = w A.x, ..., dL/dw = x A.x + y A.y + z A.z + A.w
@@ -267,16 +280,52 @@ static __device__ __noinline__ void final_reduce(const KParams& kp, int item)
             kp.adam_v[idx] = vv;
             kp.ctrl_w[idx] = cn;
         }
+    };
+    // two control points per pass; the loads of four units for both are issued
+    // before any is summed, and the sums run in unit order
+    constexpr int UB = 4;
+    for (int e0 = tid; e0 < ncp; e0 += 2 * bs) {
+        const int e1 = e0 + bs;
+        const bool has1 = e1 < ncp;
+        const int i0 = e0 / m1, j0 = e0 - i0 * m1;
+        const int i1 = e1 / m1, j1 = e1 - i1 * m1;
+        float4 a0 = f4zero(), a1 = f4zero();
+        for (int ub = 0; ub < nunits; ub += UB) {
+            float4 v0[UB], v1[UB];
+#pragma unroll
+            for (int k = 0; k < UB; ++k) {
+                v0[k] = f4zero();
+                v1[k] = f4zero();
+                const int u = ub + k;
+                if (u < nunits) {
+                    const int* h = s_units + u * 8;
+                    const int ilo = h[0], nr = h[1], jlo = h[2], cw = h[3];
+                    const long long off = (long long)(unsigned)h[6] | ((long long)h[7] << 32);
+                    const float4* A = reinterpret_cast<const float4*>(kp.part + off);
+                    if (h[4] && i0 >= ilo && i0 < ilo + nr && j0 >= jlo && j0 < jlo + cw)
+                        v0[k] = __ldcg(A + (i0 - ilo) * m1 + (j0 - jlo));
+                    if (h[4] && has1 && i1 >= ilo && i1 < ilo + nr && j1 >= jlo && j1 < jlo + cw)
+                        v1[k] = __ldcg(A + (i1 - ilo) * m1 + (j1 - jlo));
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < UB; ++k) {
+                a0.x += v0[k].x; a0.y += v0[k].y; a0.z += v0[k].z; a0.w += v0[k].w;
+                a1.x += v1[k].x; a1.y += v1[k].y; a1.z += v1[k].z; a1.w += v1[k].w;
+            }
+        }
+        finish(e0, a0);
+        if (has1) finish(e1, a1);
     }
 }
 
 // ---------------------------------------------------------------------------
 // One tile.  GRAD = false: forward only (S -> pts).  GRAD = true: recompute the
-// forward, form dL/dS (given, or from the MSE target), and write this tile's
+// forward, form dL/dS (given, or from the target when MSE), and write this tile's
 // partials; the last CTA of the item reduces them.  KNOTS adds beta / Gamma and
 // the knot partials.
 // ---------------------------------------------------------------------------
-template <int P, int Q, bool GRAD, bool KNOTS>
+template <int P, int Q, bool GRAD, bool KNOTS, bool MSE>
 __device__ __forceinline__ void tile_body(const KParams& kp, int t)
 {
     extern __shared__ float4 smem4[];
@@ -302,81 +351,162 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
     const bool empty = nrows <= 0 || ncols <= 0;   // an item without samples: zero gradients
 
     if (tid == 0) { s_flag[0] = empty ? 1 : 0; s_flag[1] = 0; }
+
+    // tile geometry: units of nwc column warps, each over a group of rows
+    const int nwc = tl.nwc, nwr = tl.nwr, rpg = tl.rpg;
+    const int wc = warp % nwc, wr = warp / nwc;
+    const int ra = wr * rpg, rb = min(nrows, ra + rpg);
+    const int wcol0 = wc * 32;
+    const int nvw = max(0, min(32, ncols - wcol0));     // valid columns of this warp
+    const int uthreads = nwc * 32, ut = wc * 32 + lane; // threads of the unit, index in it
+    const int bl = wcol0 + lane;
+    const int blc = min(bl, max(ncols - 1, 0));
+
+    // ring of incoming dL/dS (or target) rows for this warp's columns; the first
+    // rows are requested before the prologue so their latency overlaps it
+    float* ring = reinterpret_cast<float*>(smem + kp.off_ring) + warp * (kRing * 96);
+    const int nf = 3 * nvw;
+    const long long prow0 = it.pts + (long long)tl.row0 * it.nv + tl.col0 + wcol0;  // point (row 0, lane 0)
+    const float* grow0 = GRAD ? kp.gin + 3 * prow0 : nullptr;
+    const bool al16 = ((prow0 & 3) == 0) && ((it.nv & 3) == 0) && ((nvw & 3) == 0);
+    const bool wrows = !empty && wr < nwr && ra < rb;
+    // requests go out in row order: src walks the rows, dst walks the ring slots
+    const bool ring_on = wrows && nf > 0;
+    const float* isrc = ring_on ? grow0 + 3LL * ra * it.nv + (al16 ? 4 * lane : lane) : nullptr;
+    float* idst = ring + (al16 ? 4 * lane : lane);
+    const bool il16 = al16 && lane * 4 < nf;
+    auto issue = [&](int r) {
+        if (ring_on && r < rb) {
+            if (al16) {
+                if (il16) cp_async16(idst, isrc);
+            } else {
+                for (int k = 0; lane + k < nf; k += 32) cp_async4(idst + k, isrc + k);
+            }
+        }
+        cp_async_commit();
+        isrc += 3 * it.nv;
+        idst = ((r - ra) & (kRing - 1)) == kRing - 1 ? idst - (kRing - 1) * 96 : idst + 96;
+    };
+    int nexti = ra;   // next row of the ring to request
+    if constexpr (GRAD) {
+#pragma unroll
+        for (int d = 0; d < kRing - 1; ++d) issue(nexti++);
+    }
     __syncthreads();
 
-    // ---- knot-vector check, once per item
-    if (tl.tidx == 0 && !empty) {
+    // ---- stage the knot vectors and this tile's samples in shared memory (one round trip)
+    float* s_knU = reinterpret_cast<float*>(smem + kp.off_knots);
+    float* s_knV = s_knU + ((P > 0) ? ((it.n1 + P + 1 + 3) & ~3) : 0);
+    const int nU = (P > 0) ? it.n1 + P + 1 : 0, nV = it.m1 + Q + 1;
+    if (!empty) {
+        for (int k = tid; k < nU; k += bs) cp_async4(s_knU + k, U + k);
+        for (int k = tid; k < nV; k += bs) cp_async4(s_knV + k, V + k);
+        if constexpr (P > 0)
+            for (int r = tid; r < nrows; r += bs) cp_async4(s_u + r, kp.params + it.param_u + tl.row0 + r);
+        for (int c = tid; c < ncols; c += bs) cp_async4(s_v + c, kp.params + it.param_v + tl.col0 + c);
+    }
+    // the whole control net rides along when it fits (else the tile's window follows later)
+    float4* s_win = reinterpret_cast<float4*>(smem + kp.off_win);
+    const int ncp = it.n1 * it.m1;
+    const bool net_staged = !empty && ncp <= kWinCap;
+    if (net_staged) {
+        const float4* src = kp.ctrl + it.ctrl;
+        for (int e = tid; e < ncp; e += bs)
+            cp_async16(reinterpret_cast<float*>(s_win + e), reinterpret_cast<const float*>(src + e));
+    }
+    cp_async_commit();
+    cp_async_wait<0>();
+    __syncthreads();
+    if (net_staged)
+        for (int e = tid; e < ncp; e += bs) s_win[e] = homog(s_win[e]);
+
+    // ---- device checks: knot vectors once per item, samples in the domain and in order
+    if (!empty) {
         unsigned e = 0;
-        if constexpr (P > 0) {
-            for (int k = tid; k < it.n1 + P; k += bs)
-                if (__ldg(U + k) > __ldg(U + k + 1)) e |= kErrKnots;
-            if (tid == 0 && !(__ldg(U + n) < __ldg(U + n + 1))) e |= kErrKnots;
+        if (tl.tidx == 0) {
+            if constexpr (P > 0) {
+                for (int k = tid; k < nU - 1; k += bs)
+                    if (s_knU[k] > s_knU[k + 1]) e |= kErrKnots;
+                if (tid == 0 && !(s_knU[n] < s_knU[n + 1])) e |= kErrKnots;
+            }
+            for (int k = tid; k < nV - 1; k += bs)
+                if (s_knV[k] > s_knV[k + 1]) e |= kErrKnots;
+            if (tid == 0 && !(s_knV[m] < s_knV[m + 1])) e |= kErrKnots;
         }
-        for (int k = tid; k < it.m1 + Q; k += bs)
-            if (__ldg(V + k) > __ldg(V + k + 1)) e |= kErrKnots;
-        if (tid == 0 && !(__ldg(V + m) < __ldg(V + m + 1))) e |= kErrKnots;
+        if constexpr (P > 0) {
+            const float lo = s_knU[P], hi = s_knU[n + 1];
+            for (int r = tid; r < nrows; r += bs) {
+                const float u0 = s_u[r];
+                if (!(u0 >= lo && u0 <= hi)) e |= kErrDomain;
+                if (r > 0 && s_u[r - 1] > u0) e |= kErrOrder;
+            }
+        }
+        {
+            const float lo = s_knV[Q], hi = s_knV[m + 1];
+            for (int c = tid; c < ncols; c += bs) {
+                const float v0 = s_v[c];
+                if (!(v0 >= lo && v0 <= hi)) e |= kErrDomain;
+                if (c > 0 && s_v[c - 1] > v0) e |= kErrOrder;
+            }
+        }
         if (e) atomicOr(&kp.hdr->error, e);
     }
+    __syncthreads();
 
-    // ---- row prologue: span and u-basis per sample row (Sec. 3.1 steps 1-2)
-    for (int r = tid; r < nrows; r += bs) {
+    // ---- row prologue: span and u-basis per sample row (Sec. 3.1 steps 1-2);
+    // samples outside the domain are clamped to it (and reported above)
+    const int npro_r = empty ? 0 : nrows, npro_c = empty ? 0 : ncols;   // empty tiles skip the tables
+    for (int r = tid; r < npro_r; r += bs) {
         float N[PB];
         int s = 0;
         float u0 = 0.f;
         if constexpr (P > 0) {
-            const int a = tl.row0 + r;
-            u0 = __ldg(kp.params + it.param_u + a);
-            unsigned e = 0;
-            const float lo = __ldg(U + P), hi = __ldg(U + n + 1);
-            if (!(u0 >= lo && u0 <= hi)) { e |= kErrDomain; u0 = fminf(fmaxf(u0, lo), hi); }
-            if (r > 0 && __ldg(kp.params + it.param_u + a - 1) > u0) e |= kErrOrder;
-            if (e) atomicOr(&kp.hdr->error, e);
-            s = find_span(n, P, u0, U);
+            u0 = fminf(fmaxf(s_u[r], s_knU[P]), s_knU[n + 1]);
+            s = find_span(n, P, u0, s_knU);
         }
-        basis_funs<P>(s, u0, U, N);
+        basis_funs<P>(s, u0, s_knU, N);
         s_su[r] = s;
         s_u[r] = u0;
 #pragma unroll
         for (int k = 0; k < PB; ++k) s_nu[r * kMaxBasis + k] = N[k];
     }
     // ---- column prologue: span and v-basis per sample column
-    for (int c = tid; c < ncols; c += bs) {
+    for (int c = tid; c < npro_c; c += bs) {
         float N[QB];
-        const int b = tl.col0 + c;
-        float v0 = __ldg(kp.params + it.param_v + b);
-        unsigned e = 0;
-        const float lo = __ldg(V + Q), hi = __ldg(V + m + 1);
-        if (!(v0 >= lo && v0 <= hi)) { e |= kErrDomain; v0 = fminf(fmaxf(v0, lo), hi); }
-        if (c > 0 && __ldg(kp.params + it.param_v + b - 1) > v0) e |= kErrOrder;
-        if (e) atomicOr(&kp.hdr->error, e);
-        const int s = find_span(m, Q, v0, V);
-        basis_funs<Q>(s, v0, V, N);
+        const float v0 = fminf(fmaxf(s_v[c], s_knV[Q]), s_knV[m + 1]);
+        const int s = find_span(m, Q, v0, s_knV);
+        basis_funs<Q>(s, v0, s_knV, N);
         s_sv[c] = s;
         s_v[c] = v0;
 #pragma unroll
         for (int k = 0; k < QB; ++k) s_nv[c * kMaxBasis + k] = N[k];
     }
     __syncthreads();
-    // ---- the sliding windows need non-decreasing spans; anything else is refused
+    // ---- the sliding windows need non-decreasing spans; anything else is refused.
+    // Rows with equal u-span form runs; s_run[r] is the end of the run holding r.
+    int* s_run = reinterpret_cast<int*>(smem + kp.off_run);
+    int* s_crun = reinterpret_cast<int*>(smem + kp.off_crun);
     {
         bool bad = false;
-        for (int r = tid + 1; r < nrows; r += bs) bad |= s_su[r] < s_su[r - 1];
-        for (int c = tid + 1; c < ncols; c += bs) bad |= s_sv[c] < s_sv[c - 1];
+        for (int r = tid; r < npro_r; r += bs) {
+            if (r > 0) bad |= s_su[r] < s_su[r - 1];
+            int re = r + 1;
+            while (re < nrows && s_su[re] == s_su[r]) ++re;
+            s_run[r] = re;
+        }
+        for (int c = tid; c < npro_c; c += bs) {
+            if (c > 0) bad |= s_sv[c] < s_sv[c - 1];
+            int ce = c + 1;
+            while (ce < ncols && s_sv[ce] == s_sv[c]) ++ce;
+            s_crun[c] = ce;
+        }
         if (bad) { s_flag[0] = 1; atomicOr(&kp.hdr->error, kErrOrder); }
     }
     __syncthreads();
     const bool bad = s_flag[0] != 0;
 
-    const int nwc = tl.nwc, nwr = tl.nwr, rpg = tl.rpg;
-    const int wc = warp % nwc, wr = warp / nwc;
-    const int ra = wr * rpg, rb = min(nrows, ra + rpg);
-    const int wcol0 = wc * 32;
-    const int nvw = max(0, min(32, ncols - wcol0));     // valid columns of this warp
     const bool uactive = !bad && wr < nwr && ra < rb;   // the warp's unit has work
-    const int uthreads = nwc * 32, ut = wc * 32 + lane; // threads of the unit, index in it
-    const int bl = wcol0 + lane;
     const bool cvalid = uactive && lane < nvw;
-    const int blc = min(bl, ncols - 1);
 
     float* slot = GRAD ? tile_slot(kp, tl) : nullptr;
     float* uslot = GRAD ? slot + it.wbase + (long long)wr * it.unit_slot : nullptr;
@@ -390,12 +520,54 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
     // jlo_t + jj of the A contraction (all units of a tile span the same columns)
     const int jlo_t = bad ? 0 : s_sv[0] - Q;
     const int cw_t = bad ? 0 : s_sv[ncols - 1] - jlo_t + 1;
+    // The contraction A[i][j] = sum_b Nv_{j-s_v(b)+Q}(b) tau[i](b) as a fixed sparse
+    // matrix: for control column jlo_t + jj, the samples [lo, lo+len) and their weights
+    // at s_w[s_joff[jj] ...] (every sample feeds Q+1 columns, so ncols*(Q+1) weights).
     int2* s_jb = reinterpret_cast<int2*>(smem + kp.off_jb);
+    int* s_joff = reinterpret_cast<int*>(smem + kp.off_w);
+    float* s_w = reinterpret_cast<float*>(smem + kp.off_w) + kJbCap;
+    const int njb = min(cw_t, kJbCap);
     if constexpr (GRAD) {
-        for (int jj = tid; jj < min(cw_t, kJbCap); jj += bs)
-            s_jb[jj] = make_int2(lower_bound_i(s_sv, ncols, jlo_t + jj), lower_bound_i(s_sv, ncols, jlo_t + jj + Q + 1));
+        for (int jj = tid; jj < njb; jj += bs) {
+            const int lo = lower_bound_i(s_sv, ncols, jlo_t + jj);
+            s_jb[jj] = make_int2(lo, lower_bound_i(s_sv, ncols, jlo_t + jj + Q + 1) - lo);
+        }
         __syncthreads();
+        if (tid == 0) {
+            int o = 0;
+            for (int jj = 0; jj < njb; ++jj) { s_joff[jj] = o; o += s_jb[jj].y; }
+        }
+        __syncthreads();
+        for (int jj = tid; jj < njb; jj += bs) {
+            const int2 r2 = s_jb[jj];
+            const int j = jlo_t + jj;
+            float* w = s_w + s_joff[jj];
+            for (int q = 0; q < r2.y; ++q) {
+                const int b = r2.x + q;
+                w[q] = s_nv[b * kMaxBasis + (j - s_sv[b] + Q)];
+            }
+        }
     }
+    // otherwise the tile's window of control points, rows [iwl, iwl+rw) x columns
+    // [jlo_t, jlo_t+cw_t), when it fits; both are held as homogeneous points
+    const int iwl = (bad || net_staged) ? 0 : s_su[0] - P;
+    const int rw_t = bad ? 0 : s_su[nrows - 1] - (s_su[0] - P) + 1;
+    const bool win_only = !bad && !net_staged && rw_t * cw_t <= kWinCap;
+    const bool win = net_staged || win_only;
+    const int w_j0 = net_staged ? 0 : jlo_t;        // window column of element 0
+    const int w_stride = net_staged ? it.m1 : cw_t;  // window row stride
+    if (win_only) {
+        const float4* src = kp.ctrl + it.ctrl + (long long)iwl * it.m1 + jlo_t;
+        for (int e = tid; e < rw_t * cw_t; e += bs) {
+            const int ii = e / cw_t, jj = e - ii * cw_t;
+            cp_async16(reinterpret_cast<float*>(s_win + e), reinterpret_cast<const float*>(src + (long long)ii * it.m1 + jj));
+        }
+        cp_async_commit();
+        cp_async_wait<0>();
+        __syncthreads();
+        for (int e = tid; e < rw_t * cw_t; e += bs) s_win[e] = homog(s_win[e]);
+    }
+    __syncthreads();
 
     if (uactive) {
         const int svb = s_sv[blc];
@@ -406,17 +578,24 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
         const float4* __restrict__ cbase = kp.ctrl + it.ctrl + (svb - Q);  // column of h = 0
         const int m1 = it.m1;
 
+        const float4* wbase = s_win + (svb - Q - w_j0) - iwl * w_stride;   // window element (i, column of h = 0)
         auto computeQ = [&](int i) -> float4 {
-            const float4* cr = cbase + i * m1;
             float4 acc = f4zero();
+            if (win) {
+                const float4* wr_ = wbase + i * w_stride;
 #pragma unroll
-            for (int h = 0; h < QB; ++h) {
-                const float4 c = __ldg(cr + h);
-                const float wn = Nv[h] * c.w;
-                acc.x = fmaf(wn, c.x, acc.x);
-                acc.y = fmaf(wn, c.y, acc.y);
-                acc.z = fmaf(wn, c.z, acc.z);
-                acc.w += wn;
+                for (int h = 0; h < QB; ++h) acc = fma4(Nv[h], wr_[h], acc);
+            } else {
+                const float4* cr = cbase + i * m1;
+#pragma unroll
+                for (int h = 0; h < QB; ++h) {
+                    const float4 c = __ldg(cr + h);
+                    const float wn = Nv[h] * c.w;
+                    acc.x = fmaf(wn, c.x, acc.x);
+                    acc.y = fmaf(wn, c.y, acc.y);
+                    acc.z = fmaf(wn, c.z, acc.z);
+                    acc.w += wn;
+                }
             }
             return acc;
         };
@@ -431,13 +610,26 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
             const int tasks = nb * cw_t;
             for (int task = ut; task < tasks; task += uthreads) {
                 const int k = task / cw_t, jj = task - k * cw_t;
-                const int j = jlo_t + jj;
-                int lo, hi;
-                if (jj < kJbCap) { const int2 r2 = s_jb[jj]; lo = r2.x; hi = r2.y; }
-                else { lo = lower_bound_i(s_sv, ncols, j); hi = lower_bound_i(s_sv, ncols, j + Q + 1); }
-                const float4* tb = tbuf + k * uthreads;
-                float4 acc = f4zero();
-                for (int b = lo; b < hi; ++b) acc = fma4(s_nv[b * kMaxBasis + (j - s_sv[b] + Q)], tb[b], acc);
+                float4 acc;
+                if (jj < kJbCap) {
+                    const int2 r2 = s_jb[jj];
+                    const float* w = s_w + s_joff[jj];
+                    const float4* tb = tbuf + k * uthreads + r2.x;
+                    float4 a0 = f4zero(), a1 = f4zero();
+                    int q = 0;
+                    for (; q + 1 < r2.y; q += 2) {
+                        a0 = fma4(w[q], tb[q], a0);
+                        a1 = fma4(w[q + 1], tb[q + 1], a1);
+                    }
+                    if (q < r2.y) a0 = fma4(w[q], tb[q], a0);
+                    acc = make_float4(a0.x + a1.x, a0.y + a1.y, a0.z + a1.z, a0.w + a1.w);
+                } else {
+                    const int j = jlo_t + jj;
+                    const int lo = lower_bound_i(s_sv, ncols, j), hi = lower_bound_i(s_sv, ncols, j + Q + 1);
+                    const float4* tb = tbuf + k * uthreads;
+                    acc = f4zero();
+                    for (int b = lo; b < hi; ++b) acc = fma4(s_nv[b * kMaxBasis + (j - s_sv[b] + Q)], tb[b], acc);
+                }
                 uA[(nst + k) * m1 + jj] = acc;
             }
             nst += nb;
@@ -448,115 +640,133 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
         // consecutive order; rows skipped by a jump retire with tau = 0).
         auto retire = [&](int i, float4 tv) {
             if constexpr (KNOTS) {
-                const float4* cr = cbase + i * m1;
+                if (win) {
+                    const float4* wr_ = wbase + i * w_stride;
 #pragma unroll
-                for (int h = 0; h < QB; ++h) Gam[h] += dot4(tv, homog(__ldg(cr + h)));
+                    for (int h = 0; h < QB; ++h) Gam[h] += dot4(tv, wr_[h]);
+                } else {
+                    const float4* cr = cbase + i * m1;
+#pragma unroll
+                    for (int h = 0; h < QB; ++h) Gam[h] += dot4(tv, homog(__ldg(cr + h)));
+                }
             }
             if (ilo < 0) ilo = i;
             tbuf[nb * uthreads + ut] = tv;
             if (++nb == kBatch) flush();
         };
 
-        // ring of incoming dL/dS (or target) rows for this warp's columns
-        float* ring = reinterpret_cast<float*>(smem + kp.off_ring) + warp * (kRing * 96);
-        const int nf = 3 * nvw;
-        const long long prow0 = it.pts + (long long)tl.row0 * it.nv + tl.col0 + wcol0;  // point index of (ra = 0, lane 0)
-        const float* grow0 = GRAD ? kp.gin + 3 * prow0 : nullptr;
-        const bool al16 = ((prow0 & 3) == 0) && ((it.nv & 3) == 0) && ((nvw & 3) == 0);
-        auto issue = [&](int r) {
-            if (r < rb && nf > 0) {
-                float* dst = ring + ((r - ra) & (kRing - 1)) * 96;
-                const float* src = grow0 + 3LL * r * it.nv;
-                if (al16) {
-                    if (lane * 4 < nf) cp_async16(dst + lane * 4, src + lane * 4);
-                } else {
-                    for (int k = lane; k < nf; k += 32) cp_async4(dst + k, src + k);
-                }
-            }
-            cp_async_commit();
-        };
-        if constexpr (GRAD) {
-#pragma unroll
-            for (int d = 0; d < kRing - 1; ++d) issue(ra + d);
-        }
 
         float4 Qw[PB];
         float4 tau[PB];
         int cur = -1;
-        for (int r = ra; r < rb; ++r) {
-            if constexpr (GRAD) issue(r + kRing - 1);
-            const int s = s_su[r];
-            float Nu[PB];
+        // Move the window to u-span s: rows leave in increasing order (GRAD: retire them).
+        auto advance = [&](int s) {
+            if (cur < 0 || s - cur > P) {
+                if constexpr (GRAD) {
+                    if (cur >= 0) {
 #pragma unroll
-            for (int k = 0; k < PB; ++k) Nu[k] = s_nu[r * kMaxBasis + k];
-            if (s != cur) {
-                if (cur < 0 || s - cur > P) {
-                    if constexpr (GRAD) {
-                        if (cur >= 0) {
-#pragma unroll
-                            for (int k = 0; k < PB; ++k) retire(cur - P + k, tau[k]);
-                            for (int i = cur + 1; i < s - P; ++i) retire(i, f4zero());
-                        }
+                        for (int k = 0; k < PB; ++k) retire(cur - P + k, tau[k]);
+                        for (int i = cur + 1; i < s - P; ++i) retire(i, f4zero());
                     }
+                }
 #pragma unroll
-                    for (int k = 0; k < PB; ++k) { Qw[k] = computeQ(s - P + k); tau[k] = f4zero(); }
-                    cur = s;
-                } else {
-                    while (cur < s) {
-                        if constexpr (GRAD) retire(cur - P, tau[0]);
+                for (int k = 0; k < PB; ++k) { Qw[k] = computeQ(s - P + k); tau[k] = f4zero(); }
+                cur = s;
+            } else {
+                while (cur < s) {
+                    if constexpr (GRAD) retire(cur - P, tau[0]);
 #pragma unroll
-                        for (int k = 0; k < P; ++k) { Qw[k] = Qw[k + 1]; tau[k] = tau[k + 1]; }
-                        ++cur;
-                        Qw[P] = computeQ(cur);
-                        tau[P] = f4zero();
+                    for (int k = 0; k < P; ++k) { Qw[k] = Qw[k + 1]; tau[k] = tau[k + 1]; }
+                    ++cur;
+                    Qw[P] = computeQ(cur);
+                    tau[P] = f4zero();
+                }
+            }
+        };
+
+        const int rstride = 3 * it.nv;                        // floats between sample rows
+        const bool store = cvalid && kp.pts != nullptr;
+        float* orow = kp.pts != nullptr ? kp.pts + 3 * (prow0 + lane) : nullptr;   // row 0 of this lane
+        float* s_beta_w = reinterpret_cast<float*>(smem + kp.off_beta) + (wc * kp.R) * kMaxBasis;
+
+        // One or two rows (same u-span) per step: S, dL/dS, lambda, tau and beta.
+        // NR = rows in the step; the ring slots of rows < r are free for refills.
+        auto step = [&](auto nr_tag, int r) {
+            constexpr int NR = decltype(nr_tag)::value;
+            if constexpr (GRAD) {
+                while (nexti <= r + kRing - 1) issue(nexti++);
+            }
+            float Nu[NR][PB];
+#pragma unroll
+            for (int q = 0; q < NR; ++q) load_basis<PB>(s_nu + (r + q) * kMaxBasis, Nu[q]);
+            // homogeneous point and perspective divide (Sec. 3.1 step 3)
+            float Sx[NR], Sy[NR], Sz[NR], inv[NR];
+#pragma unroll
+            for (int q = 0; q < NR; ++q) {
+                float4 Sw = f4zero();
+#pragma unroll
+                for (int k = 0; k < PB; ++k) Sw = fma4(Nu[q][k], Qw[k], Sw);
+                inv[q] = rcp_approx(Sw.w);
+                Sx[q] = Sw.x * inv[q]; Sy[q] = Sw.y * inv[q]; Sz[q] = Sw.z * inv[q];
+            }
+            if constexpr (!GRAD) {
+#pragma unroll
+                for (int q = 0; q < NR; ++q) {
+                    float* o = orow + (r + q) * rstride;
+                    if (store) { o[0] = Sx[q]; o[1] = Sy[q]; o[2] = Sz[q]; }
+                }
+            } else {
+                if constexpr (NR == 2) cp_async_wait<kRing - 2>(); else cp_async_wait<kRing - 1>();
+                __syncwarp();
+                float4 lam[NR];
+#pragma unroll
+                for (int q = 0; q < NR; ++q) {
+                    const float* gp = ring + ((r + q - ra) & (kRing - 1)) * 96 + 3 * lane;
+                    float gx, gy, gz;
+                    if constexpr (MSE) {
+                        float dx = Sx[q] - gp[0], dy = Sy[q] - gp[1], dz = Sz[q] - gp[2];
+                        dx = cvalid ? dx : 0.f; dy = cvalid ? dy : 0.f; dz = cvalid ? dz : 0.f;
+                        lossacc = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, lossacc)));
+                        gx = kp.grad_scale * dx; gy = kp.grad_scale * dy; gz = kp.grad_scale * dz;
+                    } else {
+                        gx = cvalid ? gp[0] : 0.f; gy = cvalid ? gp[1] : 0.f; gz = cvalid ? gp[2] : 0.f;
+                    }
+                    float* o = orow + (r + q) * rstride;
+                    if (store) { o[0] = Sx[q]; o[1] = Sy[q]; o[2] = Sz[q]; }
+                    // lambda = dL/dS' for S' = (NR, W): (g / W, -S.g / W)
+                    const float gbx = gx * inv[q], gby = gy * inv[q], gbz = gz * inv[q];
+                    lam[q] = make_float4(gbx, gby, gbz, -fmaf(Sx[q], gbx, fmaf(Sy[q], gby, Sz[q] * gbz)));
+                }
+                __syncwarp();   // these slots are refilled by later requests
+#pragma unroll
+                for (int q = 0; q < NR; ++q)
+#pragma unroll
+                    for (int k = 0; k < PB; ++k) tau[k] = fma4(Nu[q][k], lam[q], tau[k]);
+                if constexpr (KNOTS && P > 0) {
+                    constexpr int VB = Pow2<NR * PB>::v;
+                    static_assert(VB >= NR * PB && VB <= 32, "beta reduction width");
+                    float beta[VB];
+#pragma unroll
+                    for (int v = 0; v < VB; ++v) {
+                        const int q = v / PB, k = v - (v / PB) * PB;
+                        beta[v] = v < NR * PB ? dot4(Qw[k < PB ? k : 0], lam[q < NR ? q : 0]) : 0.f;
+                    }
+                    warp_reduce_multi<VB>(beta, lane);
+                    const int idx = reduce_index<VB>(lane);
+                    if ((lane & (32 / VB - 1)) == 0 && idx < NR * PB) {
+                        const int q = idx / PB;
+                        s_beta_w[(r + q) * kMaxBasis + (idx - q * PB)] = beta[0];
                     }
                 }
             }
-            // homogeneous point and perspective divide (Sec. 3.1 step 3)
-            float4 Sw = f4zero();
-#pragma unroll
-            for (int k = 0; k < PB; ++k) Sw = fma4(Nu[k], Qw[k], Sw);
-            const float inv = __fdividef(1.f, Sw.w);
-            const float Sx = Sw.x * inv, Sy = Sw.y * inv, Sz = Sw.z * inv;
-            if constexpr (!GRAD) {
-                if (cvalid) {
-                    float* oo = kp.pts + 3 * (prow0 + lane + (long long)r * it.nv);
-                    oo[0] = Sx; oo[1] = Sy; oo[2] = Sz;
-                }
-            } else {
-                cp_async_wait<kRing - 1>();
-                __syncwarp();
-                const float* gp = ring + ((r - ra) & (kRing - 1)) * 96 + 3 * lane;
-                float gx = 0.f, gy = 0.f, gz = 0.f;
-                if (cvalid) {
-                    if (kp.gsrc == 0) {
-                        gx = gp[0]; gy = gp[1]; gz = gp[2];
-                    } else {
-                        const float dx = Sx - gp[0], dy = Sy - gp[1], dz = Sz - gp[2];
-                        lossacc = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, lossacc)));
-                        gx = kp.grad_scale * dx; gy = kp.grad_scale * dy; gz = kp.grad_scale * dz;
-                    }
-                    if (kp.pts != nullptr) {
-                        float* oo = kp.pts + 3 * (prow0 + lane + (long long)r * it.nv);
-                        oo[0] = Sx; oo[1] = Sy; oo[2] = Sz;
-                    }
-                }
-                __syncwarp();   // the slot is refilled by the next iteration's issue
-                // lambda = dL/dS' for S' = (NR, W): (g / W, -S.g / W)
-                const float gbx = gx * inv, gby = gy * inv, gbz = gz * inv;
-                const float4 lam = make_float4(gbx, gby, gbz, -fmaf(Sx, gbx, fmaf(Sy, gby, Sz * gbz)));
-#pragma unroll
-                for (int k = 0; k < PB; ++k) tau[k] = fma4(Nu[k], lam, tau[k]);
-                if constexpr (KNOTS && P > 0) {
-                    constexpr int VB = Pow2<PB>::v;
-                    float beta[VB];
-#pragma unroll
-                    for (int k = 0; k < VB; ++k) beta[k] = k < PB ? dot4(Qw[k < PB ? k : 0], lam) : 0.f;
-                    warp_reduce_multi<VB>(beta, lane);
-                    const int idx = reduce_index<VB>(lane);
-                    if ((lane & (32 / VB - 1)) == 0 && idx < PB)
-                        reinterpret_cast<float*>(smem + kp.off_beta)[(wc * kp.R + r) * kMaxBasis + idx] = beta[0];
-                }
+        };
+        {
+            int r = ra;
+            while (r < rb) {
+                const int re = min(s_run[r], rb);
+                advance(s_su[r]);
+                for (; r + 1 < re; r += 2) step(IntTag<2>{}, r);
+                if (r < re) { step(IntTag<1>{}, r); ++r; }
             }
         }
         if constexpr (GRAD) {
@@ -571,7 +781,7 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
             if constexpr (KNOTS) {
                 if (cvalid) {
                     float dk[2 * Q + 1];
-                    basis_knot_vjp<Q>(svb, vb, V, Gam, dk);
+                    basis_knot_vjp<Q>(svb, vb, s_knV, Gam, dk);
                     float* dv = reinterpret_cast<float*>(smem + kp.off_dvc) + (wr * kp.C + bl) * kMaxKnotWin;
 #pragma unroll
                     for (int k = 0; k < 2 * Q; ++k) dv[k] = dk[k];
@@ -599,58 +809,71 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
         if constexpr (KNOTS) {
             if (!bad) {
                 const int nwc_valid = (ncols + 31) / 32;
+                float* s_duc = reinterpret_cast<float*>(smem + kp.off_duc);
+                float* s_dvc = reinterpret_cast<float*>(smem + kp.off_dvc);
                 // dL/dU: per row, beta summed over the column warps in order, then the
                 // reverse-mode knot derivative of the row's basis
                 if constexpr (P > 0) {
-                    float* s_beta = reinterpret_cast<float*>(smem + kp.off_beta);
-                    float* s_duc = reinterpret_cast<float*>(smem + kp.off_duc);
+                    const float* s_beta = reinterpret_cast<const float*>(smem + kp.off_beta);
                     for (int r = tid; r < nrows; r += bs) {
                         float bsum[PB];
 #pragma unroll
                         for (int k = 0; k < PB; ++k) bsum[k] = 0.f;
-                        for (int w = 0; w < nwc_valid; ++w)
+                        for (int w = 0; w < nwc_valid; ++w) {
+                            float bw[PB];
+                            load_basis<PB>(s_beta + (w * kp.R + r) * kMaxBasis, bw);
 #pragma unroll
-                            for (int k = 0; k < PB; ++k) bsum[k] += s_beta[(w * kp.R + r) * kMaxBasis + k];
+                            for (int k = 0; k < PB; ++k) bsum[k] += bw[k];
+                        }
                         float dk[2 * P + 1];
-                        basis_knot_vjp<P>(s_su[r], s_u[r], U, bsum, dk);
+                        basis_knot_vjp<P>(s_su[r], s_u[r], s_knU, bsum, dk);
 #pragma unroll
                         for (int k = 0; k < 2 * P; ++k) s_duc[r * kMaxKnotWin + k] = dk[k];
                     }
                 }
                 __syncthreads();
+                // runs of rows (columns) share a knot window: sum each run first, in order
                 if constexpr (P > 0) {
-                    const float* s_duc = reinterpret_cast<const float*>(smem + kp.off_duc);
+                    for (int e = tid; e < nrows * 2 * P; e += bs) {
+                        const int r = e / (2 * P), k = e - r * (2 * P);
+                        if (r > 0 && s_su[r - 1] == s_su[r]) continue;   // not a run start
+                        float acc = 0.f;
+                        for (int q = r; q < s_run[r]; ++q) acc += s_duc[q * kMaxKnotWin + k];
+                        s_duc[r * kMaxKnotWin + k] = acc;
+                    }
+                }
+                for (int e = tid; e < ncols * 2 * Q; e += bs) {
+                    const int c = e / (2 * Q), k = e - c * (2 * Q);
+                    if (c > 0 && s_sv[c - 1] == s_sv[c]) continue;
+                    float acc = 0.f;
+                    for (int g = 0; g < nwr; ++g) {
+                        if (g * rpg >= nrows) break;
+                        for (int q = c; q < s_crun[c]; ++q) acc += s_dvc[(g * kp.C + q) * kMaxKnotWin + k];
+                    }
+                    s_dvc[c * kMaxKnotWin + k] = acc;   // row group 0's slot holds the run sum
+                }
+                __syncthreads();
+                if constexpr (P > 0) {
                     const int ku_lo = s_su[0] - P + 1;
                     const int nku = s_su[nrows - 1] + P - ku_lo + 1;
                     for (int K = tid; K < nku; K += bs) {
                         const int kk = ku_lo + K;
                         float acc = 0.f;
-                        for (int r = 0; r < nrows; ++r) {
-                            const int o = kk - (s_su[r] - P + 1);
-                            if (o >= 0 && o < 2 * P) acc += s_duc[r * kMaxKnotWin + o];
-                        }
+                        for (int r = lower_bound_i(s_su, nrows, kk - P); r < nrows && s_su[r] <= kk + P - 1; r = s_run[r])
+                            acc += s_duc[r * kMaxKnotWin + (kk - (s_su[r] - P + 1))];
                         slot[12 + K] = acc;
                     }
                     if (tid == 0) { sh[0] = ku_lo; sh[1] = nku; }
                 } else {
                     if (tid == 0) { sh[0] = 0; sh[1] = 0; }
                 }
-                // dL/dV: per column knot derivative, summed over row groups and columns in order
-                const float* s_dvc = reinterpret_cast<const float*>(smem + kp.off_dvc);
                 const int kv_lo = s_sv[0] - Q + 1;
                 const int nkv = s_sv[ncols - 1] + Q - kv_lo + 1;
                 for (int K = tid; K < nkv; K += bs) {
                     const int kk = kv_lo + K;
-                    const int clo = lower_bound_i(s_sv, ncols, kk - Q);
-                    const int chi = lower_bound_i(s_sv, ncols, kk + Q);
                     float acc = 0.f;
-                    for (int g = 0; g < nwr; ++g) {
-                        if (g * rpg >= nrows) break;
-                        for (int c = clo; c < chi; ++c) {
-                            const int o = kk - (s_sv[c] - Q + 1);
-                            acc += s_dvc[(g * kp.C + c) * kMaxKnotWin + o];
-                        }
-                    }
+                    for (int c = lower_bound_i(s_sv, ncols, kk - Q); c < ncols && s_sv[c] <= kk + Q - 1; c = s_crun[c])
+                        acc += s_dvc[c * kMaxKnotWin + (kk - (s_sv[c] - Q + 1))];
                     slot[12 + it.ku_cap + K] = acc;
                 }
                 if (tid == 0) { sh[2] = kv_lo; sh[3] = nkv; }
@@ -660,10 +883,11 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
         } else if (tid == 0) {
             sh[0] = 0; sh[1] = 0; sh[2] = 0; sh[3] = 0;
         }
-        // publish the partials; the last tile of the item reduces them
-        __threadfence();
+        // publish the partials (the barrier orders the CTA's writes before thread 0's
+        // device-scope fence); the last tile of the item reduces them
         __syncthreads();
         if (tid == 0) {
+            __threadfence();
             const unsigned prev = atomicAdd(kp.counts + tl.item, 1u);
             s_flag[1] = (prev + 1 == (unsigned)it.ntiles) ? 1 : 0;
         }
@@ -674,6 +898,7 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
             if (tid == 0) kp.counts[tl.item] = 0u;
         }
     }
+    cp_async_wait<0>();
     __syncthreads();
 }
 
