@@ -194,6 +194,33 @@ nurbs_status nurbs_fit_step(const nurbs_plan* plan, const float* knots, float* c
                             float grad_scale, float* loss_items, float* grad_knots,
                             nurbs_stream_t stream);
 
+/*
+ * nurbs_mse_fwd_bwd_noalloc -- the computation of nurbs_mse_fwd_bwd (same
+ * arguments, same results) for callers that cannot allocate device memory: for
+ * example a plug-in whose host application owns every device allocation, or code
+ * running where cudaMalloc is not allowed (inside a host callback, or in a process
+ * whose memory budget is fixed at start-up).  The paper has no counterpart; this
+ * entry point exists only for such integrations.
+ *   - It allocates nothing.  Its scratch is one fixed array of
+ *     NURBS_NOALLOC_SCRATCH_BYTES bytes in the library's device image; every GPU
+ *     that loads the library holds that array until the process exits.
+ *   - The plan needs no workspace and no nurbs_plan_bind.  A plan whose
+ *     nurbs_plan_workspace_size() exceeds NURBS_NOALLOC_SCRATCH_BYTES is rejected
+ *     with NURBS_ERR_WORKSPACE before any GPU work.
+ *   - All calls share the array: each call uploads the plan's tables into it and
+ *     clears its counters first, and calls that overlap on the GPU (other streams,
+ *     other host threads) race on it and give wrong results.
+ *   - The first call on a device looks up the array's device address (once per
+ *     device, with that device current); make that first call before any stream
+ *     capture.
+ */
+#define NURBS_NOALLOC_SCRATCH_BYTES (8u << 20)
+
+nurbs_status nurbs_mse_fwd_bwd_noalloc(const nurbs_plan* plan, const float* knots, const float* ctrl,
+                                       const float* params, const float* target, float* pts,
+                                       float* grad_ctrl, float* grad_knots, float* loss_items,
+                                       float grad_scale, nurbs_stream_t stream);
+
 /* Human-readable name of a status code (static string). */
 const char* nurbs_status_string(nurbs_status status);
 

@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -471,3 +472,118 @@ const char* nurbs_status_string(nurbs_status s)
 int32_t nurbs_last_cuda_error(void) { return g_last_cuda_error; }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free fused MSE forward + backward (nurbs_mse_fwd_bwd_noalloc).
+//
+// For callers that cannot allocate device memory themselves, the workspace of
+// this one entry point is a fixed array in the library's device image.  Every
+// call shares it, so each call re-uploads the plan's item and tile tables into it
+// and clears the queue/arrival counters before launching; the partial-sum slots
+// need no clearing (every slot is written before it is read).
+// ---------------------------------------------------------------------------
+namespace {
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NURBS_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kNoallocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kNoallocMaxDevices] = {};
+
+// Device address of g_noalloc_scratch on the current device, looked up once per device.
+nurbs_status noalloc_scratch(void** out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (dev < 0 || dev >= kNoallocMaxDevices) return NURBS_ERR_ARG;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (g_noalloc_ptr[dev] == nullptr) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || p == nullptr) return cuda_fail(e != cudaSuccess ? e : cudaErrorInvalidSymbol);
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return NURBS_OK;
+}
+
+}  // namespace
+
+extern "C" nurbs_status nurbs_mse_fwd_bwd_noalloc(const nurbs_plan* cpl, const float* knots, const float* ctrl,
+                                                  const float* params, const float* target, float* pts,
+                                                  float* grad_ctrl, float* grad_knots, float* loss_items,
+                                                  float grad_scale, nurbs_stream_t stream)
+{
+    if (cpl == nullptr) return NURBS_ERR_ARG;
+    if (cpl->ws_bytes > (size_t)NURBS_NOALLOC_SCRATCH_BYTES) return NURBS_ERR_WORKSPACE;
+    if (cpl->tiles.empty()) return NURBS_OK;
+    if (knots == nullptr || ctrl == nullptr || params == nullptr || target == nullptr) return NURBS_ERR_ARG;
+    if (((uintptr_t)ctrl & 15u) != 0 || ((uintptr_t)grad_ctrl & 15u) != 0) return NURBS_ERR_ARG;
+    void* scratch = nullptr;
+    nurbs_status st = noalloc_scratch(&scratch);
+    if (st != NURBS_OK) return st;
+    nurbs_plan* pl = const_cast<nurbs_plan*>(cpl);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    unsigned char* ws = static_cast<unsigned char*>(scratch);
+    // tables from the plan's host copies; header and arrival counters cleared
+    cudaError_t e = cudaMemsetAsync(ws, 0, pl->items_off, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ws + pl->items_off, pl->items.data(), sizeof(ItemDev) * pl->items.size(),
+                            cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ws + pl->tiles_off, pl->tiles.data(), sizeof(TileDev) * pl->tiles.size(),
+                            cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ws + pl->counts_off, 0, pl->part_off - pl->counts_off, s);
+    if (e != cudaSuccess) return cuda_fail(e);
+
+    KParams kp;
+    std::memset(&kp, 0, sizeof kp);
+    kp.knots = knots;
+    kp.ctrl = reinterpret_cast<const float4*>(ctrl);
+    kp.params = params;
+    kp.pts = pts;
+    kp.gin = target;
+    kp.gsrc = 1;
+    kp.grad_ctrl = reinterpret_cast<float4*>(grad_ctrl);
+    kp.grad_knots = grad_knots;
+    kp.loss_items = loss_items;
+    kp.grad_scale = grad_scale;
+    kp.items = reinterpret_cast<const ItemDev*>(ws + pl->items_off);
+    kp.tiles = reinterpret_cast<const TileDev*>(ws + pl->tiles_off);
+    kp.hdr = reinterpret_cast<WsHeader*>(ws);
+    kp.counts = reinterpret_cast<unsigned int*>(ws + pl->counts_off);
+    kp.part = reinterpret_cast<float*>(ws + pl->part_off);
+    kp.R = pl->R; kp.C = pl->C;
+    kp.off_misc = pl->off_misc; kp.off_su = pl->off_su; kp.off_u = pl->off_u; kp.off_nu = pl->off_nu;
+    kp.off_sv = pl->off_sv; kp.off_v = pl->off_v; kp.off_nv = pl->off_nv; kp.off_stage = pl->off_stage;
+    kp.off_beta = pl->off_beta; kp.off_duc = pl->off_duc; kp.off_dvc = pl->off_dvc; kp.off_ring = pl->off_ring;
+    kp.off_jb = pl->off_jb; kp.off_win = pl->off_win; kp.off_run = pl->off_run; kp.off_crun = pl->off_crun;
+    kp.off_knots = pl->off_knots; kp.off_w = pl->off_w; kp.off_acc = pl->off_acc;
+    kp.acc_cap = pl->acc_cap;
+    const int v = grad_knots != nullptr ? 4 : 3;
+    const int block = 32 * pl->warps;
+    for (PlanGroup& grp : pl->groups) {
+        KernelVariant kv = variant_for(v, grp.p, grp.q);
+        if (grp.grid[v] == 0) {
+            if (pl->smem_bytes > 48 * 1024) {
+                e = kv.set_smem(pl->smem_bytes);
+                if (e != cudaSuccess) return cuda_fail(e);
+            }
+            int occ = 0, dev = 0, sms = 0;
+            e = kv.occupancy(&occ, block, pl->smem_bytes);
+            if (e == cudaSuccess) e = cudaGetDevice(&dev);
+            if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            if (e != cudaSuccess) return cuda_fail(e);
+            if (occ < 1) return NURBS_ERR_SIZE;
+            if (pl->ctas_per_sm > 0) occ = std::min(occ, pl->ctas_per_sm);
+            grp.grid[v] = std::max(1, std::min(grp.t1 - grp.t0, occ * sms));
+        }
+        kp.t0 = grp.t0;
+        kp.t1 = grp.t1;
+        kp.queue = kp.hdr->queue + 2 * (grp.p * 5 + grp.q - 1);
+        e = kv.launch(kp, grp.grid[v], block, pl->smem_bytes, s);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    return NURBS_OK;
+}
