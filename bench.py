@@ -239,6 +239,13 @@ def run_ours(args):
         e_ms = float(tt.item())
     e2e_value = world * npts * args.steps / (e_ms / 1e3)
 
+    extras = {}
+    if rank == 0 and not args.no_extra:
+        extras["curves_fit_step"] = bench_curves(dev, max(5, args.steps // 2), args.warmup, flush, peak)
+        extras["ragged_graph"] = bench_ragged(dev, max(5, args.steps // 2), args.warmup, flush, peak)
+    if rank == 0 and args.serve:
+        extras["serving"] = bench_serve(dev, n_requests=args.serve_requests)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(budget_s=args.cpu_seconds)
@@ -261,6 +268,8 @@ def run_ours(args):
         }
         if cpu is not None:
             line["cpu_baseline"] = cpu
+        if extras:
+            line["extra"] = extras
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -287,6 +296,123 @@ def cpu_baseline(budget_s: float = 15.0):
         k += 1
     return {"value": done_pts / work_s, "unit": "pts/s", "cores": 1, "kind": "oracle",
             "sample": f"{k} of {WORKLOAD['batch']} surfaces ({done_pts} points), fwd + MSE + VJP incl. knots, FP64"}
+
+
+def _time_steps(fn, steps, warmup, flush, stream):
+    import torch
+    for _ in range(warmup):
+        flush.zero_()
+        fn()
+    torch.cuda.synchronize()
+    ms = 0.0
+    for _ in range(steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        ms += e0.elapsed_time(e1)
+    return ms / steps
+
+
+def bench_curves(dev, steps, warmup, flush, peak):
+    """4096 cubic 3-D curves, 64 control points, 1024 samples: one fused fit step
+    (forward, MSE, backward, Adam on control points and weights) per call."""
+    import torch
+    from paper_2104_14547_gb300 import batch, synth, tune
+    curves, targets = synth.cubic_curve_batch(0, 4096, 64, 1024)
+    pk = batch.pack_curves(curves)
+    tk = batch.pack_curves(targets)
+    kn, ct, pr = batch.to_device(pk, dev)
+    _, tct, _ = batch.to_device(tk, dev)
+    target = torch.empty((pk.npts, 3), device=dev)
+    batch.Plan.for_packed(tk, device=dev).eval(kn, tct, pr, target)
+    m, v = torch.zeros_like(ct), torch.zeros_like(ct)
+    loss = torch.empty(pk.count, device=dev)
+    plan = batch.Plan.for_packed(pk, device=dev, warps=8)
+    stream = torch.cuda.current_stream(dev)
+    step = [0]
+
+    def fn():
+        step[0] += 1
+        plan.fit_step(kn, ct, pr, target, m, v, step[0], lr=1e-3, loss_items=loss)
+
+    ms = _time_steps(fn, steps, warmup, flush, stream)
+    nctrl = int(pk.descs["n1"].sum())
+    abytes = 12 * pk.npts + nctrl * (16 * 2 + 32 * 2) + 4 * (len(pk.knots) + len(pk.params)) + 4 * pk.count
+    ach = abytes / (ms / 1e3) / 1e9
+    return {"workload": "4096 cubic 3-D curves, 64 control points, 1024 samples, fused fit step (fwd + MSE + bwd + Adam)",
+            "value": pk.npts / (ms / 1e3), "unit": "curve pts/s", "ms_per_step": ms,
+            "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                         "algorithmic_bytes": abytes}}
+
+
+def bench_ragged(dev, steps, warmup, flush, peak, count=1000):
+    """1000 surfaces, degrees 2..5, nets 8..64 and grids 32..256 per direction:
+    fwd + MSE + bwd through the CUDA-graph engine, against one launch per surface."""
+    import torch
+    from oracle import oracle as O  # noqa: F401  (targets come from the GPU forward below)
+    from paper_2104_14547_gb300 import batch, engine, synth
+    surfs, targets = synth.ragged_batch(0, count)
+    pk = batch.pack_surfaces(surfs)
+    tk = batch.pack_surfaces(targets)
+    kn, ct, pr = batch.to_device(pk, dev)
+    _, tct, _ = batch.to_device(tk, dev)
+    tpts = torch.empty((pk.npts, 3), device=dev)
+    batch.Plan.for_packed(tk, device=dev).eval(kn, tct, pr, tpts)
+    eng = engine.RaggedEngine(surfs, tpts.cpu().numpy(), device=dev,
+                              candidates=[(4, 16), (4, 32), (8, 32), (8, 64), (2, 32)])
+    eng.capture()
+    stream = torch.cuda.current_stream(dev)
+    ms = _time_steps(eng.replay, steps, warmup, flush, stream)
+    per = engine.PerItemEngine(eng)
+    ms_per = _time_steps(per.step, max(2, steps // 5), 1, flush, stream)
+    abytes = 0
+    for d in pk.descs:
+        nc = int(d["n1"]) * int(d["m1"])
+        abytes += 24 * int(d["nu"]) * int(d["nv"]) + 32 * nc + 8 * (int(d["n1"] + d["p"] + 1) + int(d["m1"] + d["q"] + 1)) \
+            + 4 * (int(d["nu"]) + int(d["nv"])) + 4
+    ach = abytes / (ms / 1e3) / 1e9
+    return {"workload": f"{count} ragged surfaces (p,q in 2..5, nets 8..64, grids 32..256), fwd + MSE + bwd, "
+                        f"{len(eng.groups)} degree groups on parallel streams, one CUDA graph",
+            "points": pk.npts, "value": pk.npts / (ms / 1e3), "unit": "surface pts/s", "ms_per_step": ms,
+            "per_surface_launches": {"value": pk.npts / (ms_per / 1e3), "ms_per_step": ms_per},
+            "speedup_vs_per_surface": ms_per / ms,
+            "tiles": {f"p{g['key'][0]}q{g['key'][1]}": list(g["tile"]) for g in eng.groups},
+            "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                         "algorithmic_bytes": abytes}}
+
+
+def bench_serve(dev, rates=(1000, 2000, 5000, 10000, 20000, 50000), n_requests=20000, seeds=None):
+    """Poisson streams of evaluate / fit-step requests on device-resident models
+    shaped like the ragged workload; p50/p99 latency and throughput per rate."""
+    from oracle import oracle as O  # noqa: F401
+    from paper_2104_14547_gb300 import batch, serve, synth
+    import torch
+    surfs, targets = synth.ragged_batch(7, 512)
+    srv = serve.Server(device=dev, hbm_fraction=0.3, max_wave=256)
+    tk = batch.pack_surfaces(targets)
+    kn, tct, pr = batch.to_device(tk, dev)
+    tpts = torch.empty((tk.npts, 3), device=dev)
+    batch.Plan.for_packed(tk, device=dev).eval(kn, tct, pr, tpts)
+    T = batch.unpack_points(tk, tpts.cpu().numpy())
+    mids = [srv.register(s, t) for s, t in zip(surfs, T)]
+    mids = [m for m in mids if m is not None]
+    srv.start()
+    out = []
+    try:
+        serve.poisson_run(srv, mids, 500, 2000.0, seed=99)   # warm-up
+        for k, rate in enumerate(rates):
+            lat, wall, pts, _ = serve.poisson_run(srv, mids, n_requests, float(rate), seed=k)
+            out.append({"rate_per_s": rate, "p50_ms": float(np.percentile(lat, 50) * 1e3),
+                        "p99_ms": float(np.percentile(lat, 99) * 1e3), "completed_per_s": n_requests / wall,
+                        "pts_per_s": pts / wall})
+    finally:
+        srv.stop()
+    return {"workload": f"{n_requests} requests per rate (70% evaluate / 30% fit step) on {len(mids)} resident "
+                        "models shaped like the ragged workload", "models": len(mids), "waves": srv.waves,
+            "sweep": out}
 
 
 def run_reference(args):
@@ -338,6 +464,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-extra", action="store_true", help="skip the curve and ragged workloads")
+    ap.add_argument("--serve", action="store_true", help="also run the serving sweep (Poisson arrivals)")
+    ap.add_argument("--serve-requests", type=int, default=20000)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

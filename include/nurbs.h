@@ -69,7 +69,8 @@ typedef struct nurbs_desc {
     int32_t p, q;        /* degrees */
     int32_t n1, m1;      /* control points per direction (n+1, m+1) */
     int32_t nu, nv;      /* sample counts per direction */
-    int32_t reserved0, reserved1;
+    int32_t adam_step;   /* nurbs_fit_step: this item's 1-based Adam step (0 = the call's step) */
+    int32_t reserved1;
     int64_t knot_u;      /* offset of U in knots[] (floats) */
     int64_t knot_v;      /* offset of V in knots[] (floats) */
     int64_t ctrl;        /* offset of the control net in ctrl[] (float4 elements) */
@@ -80,10 +81,10 @@ typedef struct nurbs_desc {
 
 /* Tile shape for a plan.  Zero fields take the library's defaults. */
 typedef struct nurbs_tile_cfg {
-    int32_t rows;        /* sample rows per tile (surfaces) / samples per tile (curves) */
-    int32_t warps;       /* warps per CTA (1..16) */
+    int32_t rows;        /* sample rows per tile (surfaces; curves use one row) */
+    int32_t warps;       /* warps per CTA (1..8) */
     int32_t ctas_per_sm; /* persistent CTAs per SM (0 = as many as fit) */
-    int32_t reserved;
+    int32_t max_ctas;    /* cap on the CTAs of each launch (0 = none); lets plans share the GPU */
 } nurbs_tile_cfg;
 
 /* Adam hyper-parameters (Kingma & Ba; the optimiser of Sec. 4). */
@@ -185,7 +186,8 @@ nurbs_status nurbs_mse_fwd_bwd(const nurbs_plan* plan, const float* knots, const
  *   ctrl        control nets, updated in place
  *   adam_m/v    Adam moments, float4 per control point in the ctrl layout (zero
  *               before the first step), updated in place
- *   step        1-based Adam step number (bias correction)
+ *   step        1-based Adam step number (bias correction) for items whose
+ *               descriptor has adam_step == 0; other items use their own
  *   pts, loss_items, grad_knots  as in nurbs_mse_fwd_bwd (NULL to skip)
  */
 nurbs_status nurbs_fit_step(const nurbs_plan* plan, const float* knots, float* ctrl,

@@ -78,7 +78,7 @@ class NurbsError(RuntimeError):
 # ----------------------------------------------------------------- ctypes types
 class Desc(ctypes.Structure):
     _fields_ = [("p", ctypes.c_int32), ("q", ctypes.c_int32), ("n1", ctypes.c_int32), ("m1", ctypes.c_int32),
-                ("nu", ctypes.c_int32), ("nv", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("nu", ctypes.c_int32), ("nv", ctypes.c_int32), ("adam_step", ctypes.c_int32),
                 ("reserved1", ctypes.c_int32), ("knot_u", ctypes.c_int64), ("knot_v", ctypes.c_int64),
                 ("ctrl", ctypes.c_int64), ("param_u", ctypes.c_int64), ("param_v", ctypes.c_int64),
                 ("pts", ctypes.c_int64)]
@@ -86,7 +86,7 @@ class Desc(ctypes.Structure):
 
 class TileCfg(ctypes.Structure):
     _fields_ = [("rows", ctypes.c_int32), ("warps", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("max_ctas", ctypes.c_int32)]
 
 
 class Adam(ctypes.Structure):

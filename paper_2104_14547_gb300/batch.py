@@ -32,7 +32,7 @@ class Packed:
 
 
 DESC_DTYPE = np.dtype([("p", "<i4"), ("q", "<i4"), ("n1", "<i4"), ("m1", "<i4"), ("nu", "<i4"), ("nv", "<i4"),
-                       ("r0", "<i4"), ("r1", "<i4"), ("knot_u", "<i8"), ("knot_v", "<i8"), ("ctrl", "<i8"),
+                       ("adam_step", "<i4"), ("r1", "<i4"), ("knot_u", "<i8"), ("knot_v", "<i8"), ("ctrl", "<i8"),
                        ("param_u", "<i8"), ("param_v", "<i8"), ("pts", "<i8")])
 assert DESC_DTYPE.itemsize == ctypes.sizeof(_lib.Desc)
 
@@ -128,12 +128,12 @@ class Plan:
     """A libnurbs plan for one batch layout plus its device workspace."""
 
     def __init__(self, kind: int, descs: np.ndarray, device="cuda", rows: int = 0, warps: int = 0,
-                 ctas_per_sm: int = 0):
+                 ctas_per_sm: int = 0, max_ctas: int = 0):
         self.lib = _lib.load()
         self.kind = kind
         self.descs = np.ascontiguousarray(descs, dtype=DESC_DTYPE)
         self.count = len(self.descs)
-        cfg = _lib.TileCfg(rows, warps, ctas_per_sm, 0)
+        cfg = _lib.TileCfg(rows, warps, ctas_per_sm, max_ctas)
         h = ctypes.c_void_p()
         dptr = self.descs.ctypes.data_as(ctypes.POINTER(_lib.Desc))
         _lib.check(self.lib.nurbs_plan_create(kind, dptr, self.count, ctypes.byref(cfg), ctypes.byref(h)),

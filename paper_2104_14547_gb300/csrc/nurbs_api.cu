@@ -38,6 +38,7 @@ struct nurbs_plan {
     int32_t kind;
     int32_t warps;            // warps per CTA
     int32_t ctas_per_sm;      // 0 = occupancy limit
+    int32_t max_ctas;         // 0 = no cap
     std::vector<ItemDev> items;
     std::vector<TileDev> tiles;
     int64_t points;
@@ -86,6 +87,7 @@ ItemDev make_item(int32_t kind, const nurbs_desc& d)
         it.knot_u = d.knot_u; it.knot_v = d.knot_v; it.ctrl = d.ctrl;
         it.param_u = d.param_u; it.param_v = d.param_v; it.pts = d.pts; it.curve = 0;
     }
+    it.adam_step = d.adam_step > 0 ? d.adam_step : 0;
     return it;
 }
 
@@ -109,12 +111,17 @@ nurbs_status nurbs_plan_create(int32_t kind, const nurbs_desc* h_desc, int32_t c
     pl->kind = kind;
     pl->warps = 8;
     pl->ctas_per_sm = 0;
+    pl->max_ctas = 0;
     int rows_cfg = 0;
     if (cfg != nullptr) {
-        if (cfg->warps < 0 || cfg->warps > 8 || cfg->rows < 0 || cfg->ctas_per_sm < 0) { delete pl; return NURBS_ERR_ARG; }
+        if (cfg->warps < 0 || cfg->warps > 8 || cfg->rows < 0 || cfg->ctas_per_sm < 0 || cfg->max_ctas < 0) {
+            delete pl;
+            return NURBS_ERR_ARG;
+        }
         if (cfg->warps > 0) pl->warps = cfg->warps;
         rows_cfg = cfg->rows;
         pl->ctas_per_sm = cfg->ctas_per_sm;
+        pl->max_ctas = cfg->max_ctas;
     }
     const int NW = pl->warps;
     const int maxcols = 32 * NW;
@@ -314,8 +321,14 @@ nurbs_status launch(const nurbs_plan* cpl, int v, KParams& kp, cudaStream_t s)
     for (PlanGroup& grp : pl->groups) {
         KernelVariant kv = variant_for(v, grp.p, grp.q);
         if (grp.grid[v] == 0) {
+            // the attribute is per kernel function: raise it to the device limit so that
+            // no plan lowers it under another plan's launch size
             cudaError_t e = cudaSuccess;
-            if (pl->smem_bytes > 48 * 1024) e = kv.set_smem(pl->smem_bytes);
+            if (pl->smem_bytes > 48 * 1024) {
+                int limit = 0;
+                e = kv.set_smem(&limit);
+                if (e == cudaSuccess && pl->smem_bytes > limit) return NURBS_ERR_SIZE;
+            }
             if (e != cudaSuccess) return cuda_fail(e);
             int occ = 0;
             e = kv.occupancy(&occ, block, pl->smem_bytes);
@@ -327,6 +340,7 @@ nurbs_status launch(const nurbs_plan* cpl, int v, KParams& kp, cudaStream_t s)
             if (occ < 1) return NURBS_ERR_SIZE;
             if (pl->ctas_per_sm > 0) occ = std::min(occ, pl->ctas_per_sm);
             grp.grid[v] = std::max(1, std::min(grp.t1 - grp.t0, occ * sms));
+            if (pl->max_ctas > 0) grp.grid[v] = std::min(grp.grid[v], pl->max_ctas);
         }
         kp.t0 = grp.t0;
         kp.t1 = grp.t1;
@@ -412,6 +426,8 @@ static nurbs_status grad_common(const nurbs_plan* pl, const float* knots, const 
         const double bc1 = 1.0 - std::pow((double)hp->beta1, (double)step);
         const double bc2 = 1.0 - std::pow((double)hp->beta2, (double)step);
         kp.fit = 1;
+        kp.lr = hp->lr;
+        kp.step = step;
         kp.adam_m = reinterpret_cast<float4*>(adam_m);
         kp.adam_v = reinterpret_cast<float4*>(adam_v);
         kp.lr_t = (float)(hp->lr / bc1);
@@ -567,8 +583,10 @@ extern "C" nurbs_status nurbs_mse_fwd_bwd_noalloc(const nurbs_plan* cpl, const f
         KernelVariant kv = variant_for(v, grp.p, grp.q);
         if (grp.grid[v] == 0) {
             if (pl->smem_bytes > 48 * 1024) {
-                e = kv.set_smem(pl->smem_bytes);
+                int limit = 0;
+                e = kv.set_smem(&limit);
                 if (e != cudaSuccess) return cuda_fail(e);
+                if (pl->smem_bytes > limit) return NURBS_ERR_SIZE;
             }
             int occ = 0, dev = 0, sms = 0;
             e = kv.occupancy(&occ, block, pl->smem_bytes);

@@ -33,7 +33,7 @@ __global__ void __launch_bounds__(256, 2) tiles_kernel(const __grid_constant__ K
 struct KernelVariant {
     cudaError_t (*launch)(const KParams&, int grid, int block, int smem, cudaStream_t);
     cudaError_t (*occupancy)(int* ctas_per_sm, int block, int smem);
-    cudaError_t (*set_smem)(int smem);
+    cudaError_t (*set_smem)(int* limit);
 };
 
 template <int P, int Q, bool G, bool K, bool M>
@@ -47,9 +47,18 @@ struct VariantOf {
     {
         return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, tiles_kernel<P, Q, G, K, M>, block, smem);
     }
-    static cudaError_t set_smem(int smem)
+    // Raise the kernel's dynamic shared-memory limit to what the device allows next to
+    // its static shared memory (the attribute is per function, so it is never lowered).
+    static cudaError_t set_smem(int* limit)
     {
-        return cudaFuncSetAttribute(tiles_kernel<P, Q, G, K, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        int dev = 0, optin = 0;
+        cudaFuncAttributes fa;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, tiles_kernel<P, Q, G, K, M>);
+        if (e != cudaSuccess) return e;
+        *limit = optin - (int)fa.sharedSizeBytes;
+        return cudaFuncSetAttribute(tiles_kernel<P, Q, G, K, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, *limit);
     }
     static KernelVariant get() { return KernelVariant{launch, occupancy, set_smem}; }
 };

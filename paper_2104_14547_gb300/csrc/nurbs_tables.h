@@ -40,7 +40,7 @@ struct ItemDev {
     int unit_slot;   // floats per unit slot
     int abase;       // float offset of A inside a unit slot (16-byte aligned)
     int curve;       // 1: a curve item mapped onto the v direction (p == 0, n1 == 1)
-    int pad;
+    int adam_step;   // fit step: this item's Adam step (0 = the launch's)
     long long knot_u, knot_v, ctrl, param_u, param_v, pts;
 };
 

@@ -62,9 +62,10 @@ struct KParams {
     float* loss_items;
     float4* adam_m;
     float4* adam_v;
-    float grad_scale, lr_t, inv_sqrt_bc2, b1, b2, eps;
+    float grad_scale, lr_t, inv_sqrt_bc2, b1, b2, eps, lr;
     int gsrc;
     int fit;
+    int step;                // Adam step of the launch (items may override)
     // shared-memory carve-up in bytes (host-computed for the plan's largest tile)
     int R, C;
     int off_misc, off_su, off_u, off_nu, off_sv, off_v, off_nv, off_stage, off_beta, off_duc, off_dvc, off_ring,
@@ -258,6 +259,13 @@ static __device__ __noinline__ void final_reduce(const KParams& kp, int item)
     }
     __syncthreads();
     const int m1 = it.m1, ncp = it.n1 * m1;
+    // Adam bias corrections: the launch's, or this item's own step
+    float lr_t = kp.lr_t, isb2 = kp.inv_sqrt_bc2;
+    if (kp.fit && it.adam_step > 0 && it.adam_step != kp.step) {
+        const float t = (float)it.adam_step;
+        lr_t = kp.lr / (1.f - powf(kp.b1, t));
+        isb2 = rsqrtf(1.f - powf(kp.b2, t));
+    }
     auto finish = [&](int e, float4 a) {
         const long long idx = it.ctrl + e;
         const float4 c = kp.ctrl[idx];
@@ -272,10 +280,10 @@ static __device__ __noinline__ void final_reduce(const KParams& kp, int item)
             mm.z = fmaf(kp.b1, mm.z, ob1 * g.z); vv.z = fmaf(kp.b2, vv.z, ob2 * g.z * g.z);
             mm.w = fmaf(kp.b1, mm.w, ob1 * g.w); vv.w = fmaf(kp.b2, vv.w, ob2 * g.w * g.w);
             float4 cn;
-            cn.x = c.x - kp.lr_t * mm.x / fmaf(sqrtf(vv.x), kp.inv_sqrt_bc2, kp.eps);
-            cn.y = c.y - kp.lr_t * mm.y / fmaf(sqrtf(vv.y), kp.inv_sqrt_bc2, kp.eps);
-            cn.z = c.z - kp.lr_t * mm.z / fmaf(sqrtf(vv.z), kp.inv_sqrt_bc2, kp.eps);
-            cn.w = c.w - kp.lr_t * mm.w / fmaf(sqrtf(vv.w), kp.inv_sqrt_bc2, kp.eps);
+            cn.x = c.x - lr_t * mm.x / fmaf(sqrtf(vv.x), isb2, kp.eps);
+            cn.y = c.y - lr_t * mm.y / fmaf(sqrtf(vv.y), isb2, kp.eps);
+            cn.z = c.z - lr_t * mm.z / fmaf(sqrtf(vv.z), isb2, kp.eps);
+            cn.w = c.w - lr_t * mm.w / fmaf(sqrtf(vv.w), isb2, kp.eps);
             kp.adam_m[idx] = mm;
             kp.adam_v[idx] = vv;
             kp.ctrl_w[idx] = cn;

@@ -1,0 +1,124 @@
+"""Ragged batches of surfaces in one persistent, CUDA-graph-captured launch set.
+
+A batch with mixed degrees, control nets and grids is packed once.  Items are
+grouped by degree pair; each group gets its own libnurbs plan over the shared
+packed arrays, a tile shape from the autotuner, and a CTA budget proportional to
+its share of the work, so the groups' persistent kernels run side by side on
+their own streams.  The whole step (forward + MSE + backward, or the fused fit
+step) is captured into one CUDA graph and replayed.
+
+`per_item_step` runs the same kernels with one launch per surface: the
+unbatched form the batched engine is compared against.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import _lib, batch, tune
+
+
+class RaggedEngine:
+    def __init__(self, surfaces, targets_pts: np.ndarray, device="cuda", autotune=True, knots_grad=True,
+                 candidates=None):
+        self.device = torch.device(device)
+        if self.device.index is None:
+            self.device = torch.device("cuda", torch.cuda.current_device())
+        self.packed = batch.pack_surfaces(surfaces)
+        pk = self.packed
+        self.knots, self.ctrl, self.params = batch.to_device(pk, self.device)
+        self.target = torch.from_numpy(np.ascontiguousarray(targets_pts, np.float32).reshape(-1, 3)).to(self.device)
+        assert self.target.shape[0] == pk.npts
+        self.pts = torch.empty((max(pk.npts, 1), 3), device=self.device)
+        self.grad_ctrl = torch.empty_like(self.ctrl)
+        self.grad_knots = torch.empty_like(self.knots) if knots_grad else None
+        self.loss = torch.empty(pk.count, device=self.device)
+        self.grad_scale = 2.0 / (3.0 * max(pk.npts, 1))
+        self.points = pk.npts
+        sms = torch.cuda.get_device_properties(self.device).multi_processor_count
+        # degree groups
+        keys = sorted(set(zip(pk.descs["p"].tolist(), pk.descs["q"].tolist())))
+        work = {k: 0 for k in keys}
+        for d in pk.descs:
+            work[(int(d["p"]), int(d["q"]))] += int(d["nu"]) * int(d["nv"]) + 1
+        total = sum(work.values())
+        self.groups = []
+        for k in keys:
+            sel = np.nonzero((pk.descs["p"] == k[0]) & (pk.descs["q"] == k[1]))[0]
+            sub = pk.descs[sel]
+            warps, rows = 4, 32
+            if autotune:
+                sub_packed = batch.Packed(pk.kind, sub, pk.knots, pk.ctrl, pk.params, pk.npts)
+                (warps, rows), _ = tune.autotune(sub_packed, self._tensors(), op="mse", candidates=candidates,
+                                                 reps=3, device=self.device)
+            # CTA budget: this group's share of a full wave (at least one SM's worth)
+            share = work[k] / total
+            max_ctas = max(4, int(round(share * sms * 4)))
+            plan = batch.Plan(pk.kind, sub, device=self.device, warps=warps, rows=rows, max_ctas=max_ctas)
+            # loss_items is indexed by the plan's own item order: one buffer per group
+            self.groups.append(dict(key=k, items=sel, plan=plan, tile=(warps, rows), max_ctas=max_ctas,
+                                    loss=torch.zeros(len(sel), device=self.device),
+                                    stream=torch.cuda.Stream(self.device)))
+        self.graph = None
+
+    def _tensors(self):
+        return dict(knots=self.knots, ctrl=self.ctrl, params=self.params, target=self.target, pts=self.pts,
+                    grad_ctrl=self.grad_ctrl, grad_knots=self.grad_knots, loss=self.loss)
+
+    # ------------------------------------------------------------------ step
+    def step(self):
+        """Forward + MSE + backward of every item: the groups' kernels on their own
+        streams, forked from and joined back into the current stream."""
+        main = torch.cuda.current_stream(self.device)
+        for g in self.groups:
+            g["stream"].wait_stream(main)
+        for g in self.groups:
+            with torch.cuda.stream(g["stream"]):
+                g["plan"].mse_fwd_bwd(self.knots, self.ctrl, self.params, self.target, self.pts, self.grad_ctrl,
+                                      self.grad_knots, g["loss"], self.grad_scale, stream=g["stream"])
+        for g in self.groups:
+            main.wait_stream(g["stream"])
+
+    def capture(self):
+        """Record one step into a CUDA graph (warm-up first, outside the capture)."""
+        self.step()
+        torch.cuda.synchronize(self.device)
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            self.step()
+        torch.cuda.synchronize(self.device)
+        return self.graph
+
+    def replay(self):
+        if self.graph is None:
+            self.capture()
+        self.graph.replay()
+
+    def item_losses(self) -> np.ndarray:
+        """Each item's sum of squared differences, in the packed item order."""
+        out = np.zeros(self.packed.count, np.float64)
+        for g in self.groups:
+            out[g["items"]] = g["loss"].cpu().numpy()
+        return out
+
+    def errors(self):
+        out = []
+        for g in self.groups:
+            out.append(g["plan"].get_error()[0])
+        return out
+
+
+class PerItemEngine:
+    """The same kernels, one plan and one launch per surface (the unbatched form)."""
+
+    def __init__(self, eng: RaggedEngine, warps=4, rows=32):
+        self.eng = eng
+        pk = eng.packed
+        self.plans = [batch.Plan(pk.kind, pk.descs[k: k + 1], device=eng.device, warps=warps, rows=rows)
+                      for k in range(pk.count)]
+
+    def step(self):
+        e = self.eng
+        for k, p in enumerate(self.plans):
+            p.mse_fwd_bwd(e.knots, e.ctrl, e.params, e.target, e.pts, e.grad_ctrl, e.grad_knots, e.loss[k:],
+                          e.grad_scale)

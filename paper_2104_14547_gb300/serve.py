@@ -1,0 +1,349 @@
+"""Continuous-batching server for surface evaluation and fit-step requests.
+
+Models (NURBS surfaces with a fitting target) live on the device in an arena:
+knots, control nets, samples, targets and Adam moments.  The arena is sized from
+the free HBM at start-up; registering a model succeeds only while it has room
+(admission by free HBM).  Clients submit requests that name a model:
+
+* ``eval``  -- evaluate the model's current surface on its grid; the points come back;
+* ``fit``   -- one fused step (forward, MSE against the stored target, backward,
+  Adam update of the control net in place); the loss comes back.
+
+A scheduler thread forms waves from the pending requests in arrival order.  A
+wave holds at most one request per model and as many evaluations as the output
+region has room for; requests that do not fit wait for the next wave.  Each wave
+is one libnurbs plan per kind (eval / fit) launched on its own stream; up to two
+waves are in flight at once, so requests that arrive while a wave runs start on
+the device before it finishes.  Every request records its latency (submit to
+result on the host).
+"""
+from __future__ import annotations
+
+import collections
+import threading
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+import torch
+
+from . import _lib, batch
+
+
+class RangeAllocator:
+    """First-fit free list over [0, size) (units: elements)."""
+
+    def __init__(self, size: int):
+        self.size = size
+        self.free = [(0, size)]
+
+    def alloc(self, n: int, align: int = 1):
+        for k, (o, ln) in enumerate(self.free):
+            a = (o + align - 1) // align * align
+            if a + n <= o + ln:
+                rest = []
+                if a > o:
+                    rest.append((o, a - o))
+                if a + n < o + ln:
+                    rest.append((a + n, o + ln - a - n))
+                self.free[k: k + 1] = rest
+                return a
+        return None
+
+    def release(self, off: int, n: int):
+        self.free.append((off, n))
+        self.free.sort()
+        merged = []
+        for o, ln in self.free:
+            if merged and merged[-1][0] + merged[-1][1] == o:
+                merged[-1] = (merged[-1][0], merged[-1][1] + ln)
+            else:
+                merged.append((o, ln))
+        self.free = merged
+
+    @property
+    def available(self) -> int:
+        return sum(ln for _, ln in self.free)
+
+
+@dataclass
+class Model:
+    mid: int
+    p: int
+    q: int
+    n1: int
+    m1: int
+    nu: int
+    nv: int
+    knot_u: int
+    knot_v: int
+    ctrl: int
+    param_u: int
+    param_v: int
+    target: int
+    steps: int = 0
+
+
+@dataclass
+class Request:
+    kind: str                 # "eval" or "fit"
+    model: int
+    t_submit: float = 0.0
+    t_done: float = 0.0
+    result: object = None
+    error: str | None = None  # set when the server failed the request
+    done: threading.Event = field(default_factory=threading.Event)
+
+    @property
+    def latency(self) -> float:
+        return self.t_done - self.t_submit
+
+
+class Server:
+    def __init__(self, device="cuda", hbm_fraction=0.25, max_wave=256, out_points=1 << 24, lr=1e-3,
+                 warps=4, rows=32, max_models=1 << 14):
+        self.device = torch.device(device)
+        if self.device.index is None:
+            self.device = torch.device("cuda", torch.cuda.current_device())
+        self._inflight_requests = []
+        free, _ = torch.cuda.mem_get_info(self.device)
+        budget = int(free * hbm_fraction)
+        # arena split by element size: ctrl/m/v 48 B per control point, targets 12 B per point,
+        # knots/samples 4 B each; sized for grids ~ (8 x net)^2
+        unit = 48 * 64 + 12 * 4096 + 4 * 200
+        n_units = max(64, budget // unit)
+        self.n_ctrl, self.n_pts, self.n_scalar = 64 * n_units, 4096 * n_units, 200 * n_units
+        self.ctrl = torch.zeros((self.n_ctrl, 4), device=self.device)
+        self.adam_m = torch.zeros_like(self.ctrl)
+        self.adam_v = torch.zeros_like(self.ctrl)
+        self.scalars = torch.zeros(self.n_scalar, device=self.device)   # knots and samples
+        self.target = torch.zeros((self.n_pts, 3), device=self.device)
+        self.out = [torch.zeros((out_points, 3), device=self.device) for _ in range(2)]
+        self.host_out = [torch.empty((out_points, 3), pin_memory=True) for _ in range(2)]
+        self.host_loss = [torch.empty(max_wave, pin_memory=True) for _ in range(2)]
+        self.loss = [torch.zeros(max_wave, device=self.device) for _ in range(2)]
+        self.alloc_ctrl = RangeAllocator(self.n_ctrl)
+        self.alloc_pts = RangeAllocator(self.n_pts)
+        self.alloc_scalar = RangeAllocator(self.n_scalar)
+        self.models: dict[int, Model] = {}
+        self.max_wave = max_wave
+        self.out_points = out_points
+        self.lr = lr
+        self.tile = dict(warps=warps, rows=rows)
+        self.streams = [(torch.cuda.Stream(self.device), torch.cuda.Stream(self.device)) for _ in range(2)]
+        self.queue: collections.deque[Request] = collections.deque()
+        self.cv = threading.Condition()
+        self.running = False
+        self.thread = None
+        self.waves = 0
+        self.points_done = 0
+        self.failure: str | None = None
+
+    # ------------------------------------------------------------ models
+    def register(self, surface, target_pts: np.ndarray) -> int | None:
+        """Place a model in the arena; None when it does not fit (admission by free HBM)."""
+        s = surface
+        n1, m1 = s.ctrl.shape[0], s.ctrl.shape[1]
+        nk, ns, npts = len(s.U) + len(s.V), len(s.u) + len(s.v), len(s.u) * len(s.v)
+        c = self.alloc_ctrl.alloc(n1 * m1)
+        if c is None:
+            return None
+        t = self.alloc_pts.alloc(npts)
+        if t is None:
+            self.alloc_ctrl.release(c, n1 * m1)
+            return None
+        k = self.alloc_scalar.alloc(nk + ns)
+        if k is None:
+            self.alloc_ctrl.release(c, n1 * m1)
+            self.alloc_pts.release(t, npts)
+            return None
+        dev = self.device
+        self.ctrl[c: c + n1 * m1] = torch.from_numpy(np.asarray(s.ctrl, np.float32).reshape(-1, 4)).to(dev)
+        self.adam_m[c: c + n1 * m1] = 0
+        self.adam_v[c: c + n1 * m1] = 0
+        self.scalars[k: k + nk + ns] = torch.from_numpy(
+            np.concatenate([s.U, s.V, s.u, s.v]).astype(np.float32)).to(dev)
+        self.target[t: t + npts] = torch.from_numpy(np.asarray(target_pts, np.float32).reshape(-1, 3)).to(dev)
+        mid = len(self.models)
+        self.models[mid] = Model(mid, s.p, s.q, n1, m1, len(s.u), len(s.v), k, k + len(s.U), c,
+                                 k + nk, k + nk + len(s.u), t)
+        return mid
+
+    # ------------------------------------------------------------ requests
+    def submit(self, req: Request) -> Request:
+        req.t_submit = time.perf_counter()
+        if self.failure is not None:
+            req.error = self.failure
+            req.done.set()
+            return req
+        with self.cv:
+            self.queue.append(req)
+            self.cv.notify()
+        return req
+
+    def start(self):
+        self.running = True
+        self.thread = threading.Thread(target=self._loop, daemon=True)
+        self.thread.start()
+
+    def stop(self):
+        with self.cv:
+            self.running = False
+            self.cv.notify()
+        if self.thread is not None:
+            self.thread.join()
+
+    def _form_wave(self, busy: set):
+        """Pending requests admitted into one wave (arrival order, one per model,
+        evaluation outputs while the output region has room)."""
+        evals, fits, out_used, keep = [], [], 0, collections.deque()
+        while self.queue and len(evals) + len(fits) < self.max_wave:
+            r = self.queue.popleft()
+            m = self.models[r.model]
+            if r.model in busy:
+                keep.append(r)
+                continue
+            if r.kind == "eval":
+                n = m.nu * m.nv
+                if out_used + n > self.out_points:
+                    keep.append(r)
+                    break
+                evals.append((r, out_used))
+                out_used += n
+            else:
+                fits.append(r)
+            busy.add(r.model)
+        while keep:
+            self.queue.appendleft(keep.pop())
+        return evals, fits
+
+    def _descs(self, entries, fit: bool):
+        d = np.zeros(len(entries), batch.DESC_DTYPE)
+        for k, e in enumerate(entries):
+            r, off = (e, None) if fit else e
+            m = self.models[r.model]
+            d[k] = (m.p, m.q, m.n1, m.m1, m.nu, m.nv, (m.steps + 1) if fit else 0, 0,
+                    m.knot_u, m.knot_v, m.ctrl, m.param_u, m.param_v, m.target if fit else off)
+        return d
+
+    def _launch(self, slot, evals, fits):
+        se, sf = self.streams[slot]
+        main = torch.cuda.current_stream(self.device)
+        # plans first: their workspaces are cleared and bound on the current stream
+        pe = batch.Plan(_lib.KIND_SURFACE, self._descs(evals, False), device=self.device, **self.tile) if evals else None
+        pf = batch.Plan(_lib.KIND_SURFACE, self._descs(fits, True), device=self.device, **self.tile) if fits else None
+        se.wait_stream(main)
+        sf.wait_stream(main)
+        plans = []
+        n_out = 0
+        if evals:
+            pe.eval(self.scalars, self.ctrl, self.scalars, self.out[slot], stream=se)
+            n_out = sum(self.models[r.model].nu * self.models[r.model].nv for r, _ in evals)
+            with torch.cuda.stream(se):
+                self.host_out[slot][:n_out].copy_(self.out[slot][:n_out], non_blocking=True)
+            plans.append(pe)
+        if fits:
+            npts = sum(self.models[r.model].nu * self.models[r.model].nv for r in fits)
+            pf.fit_step(self.scalars, self.ctrl, self.scalars, self.target, self.adam_m, self.adam_v, 1,
+                        lr=self.lr, loss_items=self.loss[slot], grad_scale=2.0 / (3.0 * max(npts, 1)), stream=sf)
+            with torch.cuda.stream(sf):
+                self.host_loss[slot][: len(fits)].copy_(self.loss[slot][: len(fits)], non_blocking=True)
+            plans.append(pf)
+        ev = torch.cuda.Event()
+        ev.record(se)
+        ev2 = torch.cuda.Event()
+        ev2.record(sf)
+        return dict(slot=slot, evals=evals, fits=fits, plans=plans, events=(ev, ev2), n_out=n_out)
+
+    def _complete(self, w, busy: set):
+        for e in w["events"]:
+            e.synchronize()
+        now = time.perf_counter()
+        ho = self.host_out[w["slot"]]
+        for r, off in w["evals"]:
+            m = self.models[r.model]
+            n = m.nu * m.nv
+            r.result = ho[off: off + n].numpy().reshape(m.nu, m.nv, 3).copy()
+            self.points_done += n
+        hl = self.host_loss[w["slot"]]
+        for k, r in enumerate(w["fits"]):
+            m = self.models[r.model]
+            m.steps += 1
+            r.result = float(hl[k]) / (3.0 * m.nu * m.nv)
+            self.points_done += m.nu * m.nv
+        for r, _ in w["evals"]:
+            busy.discard(r.model)
+            r.t_done = now
+            r.done.set()
+        for r in w["fits"]:
+            busy.discard(r.model)
+            r.t_done = now
+            r.done.set()
+
+    def _loop(self):
+        try:
+            self._serve()
+        except BaseException as exc:  # fail every waiting request instead of leaving it hanging
+            import traceback
+            self.failure = "".join(traceback.format_exception(exc))
+            with self.cv:
+                pending = list(self.queue)
+                self.queue.clear()
+                self.running = False
+            for r in pending + self._inflight_requests:
+                if not r.done.is_set():
+                    r.error = self.failure
+                    r.done.set()
+
+    def _serve(self):
+        torch.cuda.set_device(self.device)
+        inflight: collections.deque = collections.deque()
+        self._inflight_requests = []
+        busy: set = set()
+        slot = 0
+        while True:
+            with self.cv:
+                while self.running and not self.queue and not inflight:
+                    self.cv.wait(timeout=0.05)
+                if not self.running and not self.queue and not inflight:
+                    return
+                wave = self._form_wave(busy) if len(inflight) < 2 and self.queue else ([], [])
+            evals, fits = wave
+            if evals or fits:
+                self._inflight_requests = [r for r, _ in evals] + list(fits) + \
+                    [r for r in self._inflight_requests if not r.done.is_set()]
+                inflight.append(self._launch(slot, evals, fits))
+                slot ^= 1
+                self.waves += 1
+            elif inflight:
+                self._complete(inflight.popleft(), busy)
+                continue
+            # retire finished waves without blocking the next launch
+            while inflight and (len(inflight) == 2 or all(e.query() for e in inflight[0]["events"])):
+                self._complete(inflight.popleft(), busy)
+
+
+def poisson_run(server: Server, model_ids, n_requests: int, rate: float, eval_frac: float = 0.7, seed: int = 0):
+    """Submit n_requests with exponential inter-arrival times at `rate` per second;
+    returns (latencies in seconds, wall seconds, points processed)."""
+    rng = np.random.default_rng(seed)
+    gaps = rng.exponential(1.0 / rate, size=n_requests)
+    kinds = rng.random(n_requests) < eval_frac
+    mids = rng.choice(model_ids, size=n_requests)
+    reqs = []
+    p0 = server.points_done
+    t0 = time.perf_counter()
+    t_next = t0
+    for k in range(n_requests):
+        t_next += gaps[k]
+        while True:
+            dt = t_next - time.perf_counter()
+            if dt <= 0:
+                break
+            time.sleep(min(dt, 0.001) if dt > 2e-4 else 0)
+        reqs.append(server.submit(Request("eval" if kinds[k] else "fit", int(mids[k]))))
+    for r in reqs:
+        if not r.done.wait(timeout=120.0) or r.error is not None:
+            raise RuntimeError(f"request not served: {r.error or 'timeout'}")
+    wall = time.perf_counter() - t0
+    return np.array([r.latency for r in reqs]), wall, server.points_done - p0, reqs

@@ -1,0 +1,107 @@
+"""Ragged batches through the multi-stream, CUDA-graph engine; the per-surface
+form; and the continuous-batching server (results identical alone and in the mix)."""
+import numpy as np
+import pytest
+import torch
+
+from gpu_util import G_TOL, S_TOL, bbox_diag, rel_inf
+from oracle import oracle as O
+from paper_2104_14547_gb300 import batch, engine, serve, synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _ragged(seed, n):
+    surfs, tg = synth.ragged_batch(seed, batch=n, deg=(2, 5), net=(8, 24), grid=(20, 70))
+    T = np.concatenate([O.surface_eval(t.p, t.q, t.U, t.V, t.ctrl, t.u, t.v).reshape(-1, 3) for t in tg])
+    return surfs, T
+
+
+def test_engine_graph_matches_oracle_and_eager():
+    surfs, T = _ragged(41, 14)
+    eng = engine.RaggedEngine(surfs, T, candidates=[(4, 16), (4, 32), (2, 32)])
+    assert len(eng.groups) > 1
+    eng.step()
+    torch.cuda.synchronize()
+    eager = (eng.pts.clone(), eng.grad_ctrl.clone(), eng.grad_knots.clone())
+    eng.capture()
+    eng.pts.zero_(); eng.grad_ctrl.zero_(); eng.grad_knots.zero_()
+    eng.replay()
+    torch.cuda.synchronize()
+    assert all(e == 0 for e in eng.errors())
+    for a, b in zip(eager, (eng.pts, eng.grad_ctrl, eng.grad_knots)):
+        assert torch.equal(a, b)
+    pk = eng.packed
+    S = batch.unpack_points(pk, eng.pts.cpu().numpy())
+    dc = batch.unpack_ctrl(pk, eng.grad_ctrl.cpu().numpy())
+    dk = batch.unpack_knots(pk, eng.grad_knots.cpu().numpy())
+    Tk = batch.unpack_points(pk, T)
+    losses = eng.item_losses()
+    for k, s in enumerate(surfs):
+        ref = O.surface_eval(s.p, s.q, s.U, s.V, s.ctrl, s.u, s.v)
+        assert np.abs(S[k] - ref).max() <= S_TOL * bbox_diag(s.ctrl)
+        L, g = O.mse(ref, Tk[k].astype(np.float64), 3 * pk.npts)
+        rc, rU, rV = O.surface_vjp(s.p, s.q, s.U, s.V, s.ctrl, s.u, s.v, g)
+        assert rel_inf(dc[k], rc) <= G_TOL
+        assert rel_inf(dk[k][0], rU) <= G_TOL and rel_inf(dk[k][1], rV) <= G_TOL
+        assert abs(losses[k] - L * 3 * pk.npts) <= 1e-4 * max(L * 3 * pk.npts, 1e-12)
+
+
+def test_per_item_form_matches_batched():
+    surfs, T = _ragged(42, 6)
+    eng = engine.RaggedEngine(surfs, T, autotune=False)
+    eng.step()
+    torch.cuda.synchronize()
+    ref = eng.grad_ctrl.clone()
+    per = engine.PerItemEngine(eng)
+    eng.grad_ctrl.zero_()
+    per.step()
+    torch.cuda.synchronize()
+    # same tile shape (4 warps, 32 rows) alone and in the batch: identical bits
+    assert torch.equal(ref, eng.grad_ctrl)
+
+
+def _wait(r):
+    assert r.done.wait(timeout=60.0), "request not served within 60 s"
+    assert r.error is None, r.error
+
+
+def test_server_results_same_alone_and_in_the_mix():
+    rng = np.random.default_rng(43)
+    srv = serve.Server(hbm_fraction=0.02, max_wave=64, out_points=1 << 20)
+    mids, surfs = [], []
+    for k in range(10):
+        p, q = int(rng.integers(2, 6)), int(rng.integers(2, 6))
+        s = synth.surface(rng, p, q, int(rng.integers(p + 1, 20)), int(rng.integers(q + 1, 20)),
+                          int(rng.integers(8, 60)), int(rng.integers(8, 60)))
+        t = synth.twin_net(rng, s)
+        mids.append(srv.register(s, O.surface_eval(t.p, t.q, t.U, t.V, t.ctrl, t.u, t.v)))
+        surfs.append(s)
+    assert all(m is not None for m in mids)
+    srv.start()
+    try:
+        # alone: one request at a time
+        alone = {}
+        for m in mids[:4]:
+            r = srv.submit(serve.Request("eval", m))
+            _wait(r)
+            alone[m] = r.result
+        # in the mix: evaluations of those models among fit steps on the others
+        reqs = [srv.submit(serve.Request("fit", m)) for m in mids[4:]]
+        reqs += [srv.submit(serve.Request("eval", m)) for m in mids[:4]]
+        for r in reqs:
+            _wait(r)
+        for r in reqs[len(mids) - 4:]:
+            assert np.array_equal(r.result, alone[r.model])
+            s = surfs[mids.index(r.model)]
+            ref = O.surface_eval(s.p, s.q, s.U, s.V, s.ctrl, s.u, s.v)
+            assert np.abs(r.result - ref).max() <= S_TOL * bbox_diag(s.ctrl)
+        # fit steps lower each model's loss
+        first = {r.model: r.result for r in reqs[: len(mids) - 4]}
+        again = [srv.submit(serve.Request("fit", m)) for m in mids[4:] for _ in range(20)]
+        for r in again:
+            _wait(r)
+        last = {r.model: r.result for r in again}
+        assert all(last[m] < first[m] for m in mids[4:])
+    finally:
+        srv.stop()
