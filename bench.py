@@ -330,7 +330,7 @@ def bench_curves(dev, steps, warmup, flush, peak):
     batch.Plan.for_packed(tk, device=dev).eval(kn, tct, pr, target)
     m, v = torch.zeros_like(ct), torch.zeros_like(ct)
     loss = torch.empty(pk.count, device=dev)
-    plan = batch.Plan.for_packed(pk, device=dev, warps=8)
+    plan = batch.Plan.for_packed(pk, device=dev, warps=4)
     stream = torch.cuda.current_stream(dev)
     step = [0]
 
@@ -362,7 +362,7 @@ def bench_ragged(dev, steps, warmup, flush, peak, count=1000):
     tpts = torch.empty((pk.npts, 3), device=dev)
     batch.Plan.for_packed(tk, device=dev).eval(kn, tct, pr, tpts)
     eng = engine.RaggedEngine(surfs, tpts.cpu().numpy(), device=dev,
-                              candidates=[(4, 16), (4, 32), (8, 32), (8, 64), (2, 32)])
+                              candidates=[(4, 16), (4, 32), (4, 64), (2, 32)])
     eng.capture()
     stream = torch.cuda.current_stream(dev)
     ms = _time_steps(eng.replay, steps, warmup, flush, stream)

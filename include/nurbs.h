@@ -82,7 +82,7 @@ typedef struct nurbs_desc {
 /* Tile shape for a plan.  Zero fields take the library's defaults. */
 typedef struct nurbs_tile_cfg {
     int32_t rows;        /* sample rows per tile (surfaces; curves use one row) */
-    int32_t warps;       /* warps per CTA (1..8) */
+    int32_t warps;       /* warps per CTA (1..8; default 8) */
     int32_t ctas_per_sm; /* persistent CTAs per SM (0 = as many as fit) */
     int32_t max_ctas;    /* cap on the CTAs of each launch (0 = none); lets plans share the GPU */
 } nurbs_tile_cfg;

@@ -20,6 +20,13 @@ thread_local int32_t g_last_cuda_error = 0;
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 inline int align4(int x) { return (x + 3) & ~3; }
 
+// Shared adjoint of a single-tile item: the n1 x m1 block plus (p+1) overflow
+// rows per row group.
+inline size_t smem_adjoint_bytes(const ItemDev& it, int nwr)
+{
+    return 16 * ((size_t)it.n1 * it.m1 + (size_t)nwr * (it.p + 1) * it.m1);
+}
+
 nurbs_status cuda_fail(cudaError_t e)
 {
     g_last_cuda_error = (int32_t)e;
@@ -45,8 +52,9 @@ struct nurbs_plan {
     // shared memory carve-up
     int R, C, acc_cap;
     int off_misc, off_su, off_u, off_nu, off_sv, off_v, off_nv, off_stage, off_beta, off_duc, off_dvc, off_ring,
-        off_jb, off_win, off_run, off_crun, off_knots, off_w, off_acc;
-    int smem_bytes;
+        off_jb, off_win, off_run, off_crun, off_knots, off_w, off_acc, off_sa;
+    int smem_bytes;           // gradient kernels
+    int smem_eval;            // forward kernels (no shared adjoint)
     // workspace layout (bytes)
     size_t items_off, tiles_off, counts_off, part_off, ws_bytes;
     // binding
@@ -183,6 +191,8 @@ nurbs_status nurbs_plan_create(int32_t kind, const nurbs_desc* h_desc, int32_t c
                 }
             }
             it.ntiles = ntl;
+            // single-tile items keep their adjoint in shared memory when it fits
+            it.smemA = (ntl == 1 && smem_adjoint_bytes(it, nwr) <= (size_t)kSmemACap) ? 1 : 0;
         }
         grp.t1 = (int)pl->tiles.size();
         if (grp.t1 > grp.t0) pl->groups.push_back(grp);
@@ -201,14 +211,22 @@ nurbs_status nurbs_plan_create(int32_t kind, const nurbs_desc* h_desc, int32_t c
     pl->off_misc = take(256);
     pl->off_su = take(4 * maxR);
     pl->off_u = take(4 * maxR);
-    pl->off_nu = take(4 * maxR * kMaxBasis);
+    // per-degree table strides (the kernels' SU, SV, KU, KV)
+    int su = 4, sv = 4, ku = 1, kv = 2;
+    for (const ItemDev& it : pl->items) {
+        su = std::max(su, align4(it.p + 1));
+        sv = std::max(sv, align4(it.q + 1));
+        ku = std::max(ku, 2 * it.p);
+        kv = std::max(kv, 2 * it.q);
+    }
+    pl->off_nu = take(4 * maxR * su);
     pl->off_sv = take(4 * maxC);
     pl->off_v = take(4 * maxC);
-    pl->off_nv = take(4 * maxC * kMaxBasis);
+    pl->off_nv = take(4 * maxC * sv);
     pl->off_stage = take(16 * kBatch * max_unit_cols);
-    pl->off_beta = take(4 * max_nwc * maxR * kMaxBasis);
-    pl->off_duc = take(4 * maxR * kMaxKnotWin);
-    pl->off_dvc = take(4 * max_nwr * maxC * kMaxKnotWin);
+    pl->off_beta = take(4 * max_nwc * maxR * su);
+    pl->off_duc = take(4 * maxR * ku);
+    pl->off_dvc = take(4 * max_nwr * maxC * kv);
     pl->off_ring = take(4 * NW * kRing * 96);   // only the grad kernels use it
     pl->off_jb = take(8 * kJbCap);
     pl->off_win = take(16 * kWinCap);
@@ -218,7 +236,12 @@ nurbs_status nurbs_plan_create(int32_t kind, const nurbs_desc* h_desc, int32_t c
     for (const ItemDev& it : pl->items)
         max_knots = std::max(max_knots, align4(it.n1 + it.p + 1) + it.m1 + it.q + 1);
     pl->off_knots = take(4 * max_knots);
-    pl->off_w = take(4 * (kJbCap + maxC * kMaxBasis));
+    pl->off_w = take(4 * (kJbCap + maxC * sv));
+    size_t sa_bytes = 0;
+    for (const ItemDev& it : pl->items)
+        if (it.smemA) sa_bytes = std::max(sa_bytes, smem_adjoint_bytes(it, pl->tiles[it.first_tile].nwr));
+    pl->smem_eval = (int)off;     // the forward kernels stop here
+    pl->off_sa = take(sa_bytes);
     pl->off_acc = pl->off_su;     // the final reduction reuses the tile tables
     int max_units = 1;
     for (const ItemDev& it : pl->items) {
@@ -314,24 +337,25 @@ nurbs_status launch(const nurbs_plan* cpl, int v, KParams& kp, cudaStream_t s)
     kp.R = pl->R; kp.C = pl->C;
     kp.off_misc = pl->off_misc; kp.off_su = pl->off_su; kp.off_u = pl->off_u; kp.off_nu = pl->off_nu;
     kp.off_sv = pl->off_sv; kp.off_v = pl->off_v; kp.off_nv = pl->off_nv; kp.off_stage = pl->off_stage;
-    kp.off_beta = pl->off_beta; kp.off_duc = pl->off_duc; kp.off_dvc = pl->off_dvc; kp.off_ring = pl->off_ring; kp.off_jb = pl->off_jb; kp.off_win = pl->off_win; kp.off_run = pl->off_run; kp.off_crun = pl->off_crun; kp.off_knots = pl->off_knots; kp.off_w = pl->off_w;
+    kp.off_beta = pl->off_beta; kp.off_duc = pl->off_duc; kp.off_dvc = pl->off_dvc; kp.off_ring = pl->off_ring; kp.off_jb = pl->off_jb; kp.off_win = pl->off_win; kp.off_run = pl->off_run; kp.off_crun = pl->off_crun; kp.off_knots = pl->off_knots; kp.off_w = pl->off_w; kp.off_sa = pl->off_sa;
     kp.off_acc = pl->off_acc;
     kp.acc_cap = pl->acc_cap;
     const int block = 32 * pl->warps;
+    const int smem = v == 0 ? pl->smem_eval : pl->smem_bytes;
     for (PlanGroup& grp : pl->groups) {
         KernelVariant kv = variant_for(v, grp.p, grp.q);
         if (grp.grid[v] == 0) {
             // the attribute is per kernel function: raise it to the device limit so that
             // no plan lowers it under another plan's launch size
             cudaError_t e = cudaSuccess;
-            if (pl->smem_bytes > 48 * 1024) {
+            if (smem > 48 * 1024) {
                 int limit = 0;
                 e = kv.set_smem(&limit);
-                if (e == cudaSuccess && pl->smem_bytes > limit) return NURBS_ERR_SIZE;
+                if (e == cudaSuccess && smem > limit) return NURBS_ERR_SIZE;
             }
             if (e != cudaSuccess) return cuda_fail(e);
             int occ = 0;
-            e = kv.occupancy(&occ, block, pl->smem_bytes);
+            e = kv.occupancy(&occ, block, smem);
             if (e != cudaSuccess) return cuda_fail(e);
             int dev = 0, sms = 0;
             e = cudaGetDevice(&dev);
@@ -345,7 +369,7 @@ nurbs_status launch(const nurbs_plan* cpl, int v, KParams& kp, cudaStream_t s)
         kp.t0 = grp.t0;
         kp.t1 = grp.t1;
         kp.queue = kp.hdr->queue + 2 * (grp.p * 5 + grp.q - 1);
-        cudaError_t e = kv.launch(kp, grp.grid[v], block, pl->smem_bytes, s);
+        cudaError_t e = kv.launch(kp, grp.grid[v], block, smem, s);
         if (e != cudaSuccess) return cuda_fail(e);
     }
     return NURBS_OK;
@@ -575,7 +599,7 @@ extern "C" nurbs_status nurbs_mse_fwd_bwd_noalloc(const nurbs_plan* cpl, const f
     kp.off_sv = pl->off_sv; kp.off_v = pl->off_v; kp.off_nv = pl->off_nv; kp.off_stage = pl->off_stage;
     kp.off_beta = pl->off_beta; kp.off_duc = pl->off_duc; kp.off_dvc = pl->off_dvc; kp.off_ring = pl->off_ring;
     kp.off_jb = pl->off_jb; kp.off_win = pl->off_win; kp.off_run = pl->off_run; kp.off_crun = pl->off_crun;
-    kp.off_knots = pl->off_knots; kp.off_w = pl->off_w; kp.off_acc = pl->off_acc;
+    kp.off_knots = pl->off_knots; kp.off_w = pl->off_w; kp.off_sa = pl->off_sa; kp.off_acc = pl->off_acc;
     kp.acc_cap = pl->acc_cap;
     const int v = grad_knots != nullptr ? 4 : 3;
     const int block = 32 * pl->warps;

@@ -41,6 +41,8 @@ struct ItemDev {
     int abase;       // float offset of A inside a unit slot (16-byte aligned)
     int curve;       // 1: a curve item mapped onto the v direction (p == 0, n1 == 1)
     int adam_step;   // fit step: this item's Adam step (0 = the launch's)
+    int smemA;       // single-tile item whose homogeneous adjoint stays in shared memory
+    int pad2;
     long long knot_u, knot_v, ctrl, param_u, param_v, pts;
 };
 

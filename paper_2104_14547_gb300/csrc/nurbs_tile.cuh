@@ -38,10 +38,11 @@ enum : unsigned {
 
 constexpr int kMaxBasis = 8;    // basis table stride: (max degree + 1) rounded up to a float4 pair
 constexpr int kMaxKnotWin = 10; // 2 * max degree
-constexpr int kRing = 16;       // rows of dL/dS (or target) in flight per warp (power of two)
+constexpr int kRing = 8;        // rows of dL/dS (or target) in flight per warp (power of two)
 constexpr int kBatch = 4;       // retired control rows contracted together
 constexpr int kJbCap = 256;     // column ranges cached per tile
 constexpr int kWinCap = 1024;   // control points staged in shared memory (whole net, else the tile's window)
+constexpr int kSmemACap = 40 * 1024;   // bytes of shared adjoint per single-tile item
 
 struct KParams {
     const ItemDev* items;
@@ -69,7 +70,7 @@ struct KParams {
     // shared-memory carve-up in bytes (host-computed for the plan's largest tile)
     int R, C;
     int off_misc, off_su, off_u, off_nu, off_sv, off_v, off_nv, off_stage, off_beta, off_duc, off_dvc, off_ring,
-        off_jb, off_win, off_run, off_crun, off_knots, off_w, off_acc;
+        off_jb, off_win, off_run, off_crun, off_knots, off_w, off_acc, off_sa;
 
     int acc_cap;             // bytes available to the final reduction from off_acc
 };
@@ -187,12 +188,92 @@ __device__ __forceinline__ int lower_bound_i(const int* a, int n, int key)
 
 __device__ __forceinline__ float* tile_slot(const KParams& kp, const TileDev& tl) { return kp.part + tl.part; }
 
+// Adam bias corrections: the launch's, or this item's own step.
+__device__ __forceinline__ void adam_corrections(const KParams& kp, const ItemDev& it, float& lr_t, float& isb2)
+{
+    lr_t = kp.lr_t;
+    isb2 = kp.inv_sqrt_bc2;
+    if (kp.fit && it.adam_step > 0 && it.adam_step != kp.step) {
+        const float t = (float)it.adam_step;
+        lr_t = kp.lr / (1.f - powf(kp.b1, t));
+        isb2 = rsqrtf(1.f - powf(kp.b2, t));
+    }
+}
+
+// Control point e of an item from its homogeneous adjoint a: Cartesian gradient
+// and, in a fit step, the Adam update of the point, its weight and the moments.
+__device__ __forceinline__ void finish_ctrl(const KParams& kp, const ItemDev& it, int e, float4 a, float lr_t,
+                                            float isb2)
+{
+    const long long idx = it.ctrl + e;
+    const float4 c = kp.ctrl[idx];
+    // Pw = (w x, w y, w z, w): dL/dx = w A.x, ..., dL/dw = x A.x + y A.y + z A.z + A.w
+    const float4 g = make_float4(c.w * a.x, c.w * a.y, c.w * a.z, fmaf(c.x, a.x, fmaf(c.y, a.y, fmaf(c.z, a.z, a.w))));
+    if (kp.grad_ctrl != nullptr) kp.grad_ctrl[idx] = g;
+    if (kp.fit) {
+        float4 mm = kp.adam_m[idx], vv = kp.adam_v[idx];
+        const float ob1 = 1.f - kp.b1, ob2 = 1.f - kp.b2;
+        mm.x = fmaf(kp.b1, mm.x, ob1 * g.x); vv.x = fmaf(kp.b2, vv.x, ob2 * g.x * g.x);
+        mm.y = fmaf(kp.b1, mm.y, ob1 * g.y); vv.y = fmaf(kp.b2, vv.y, ob2 * g.y * g.y);
+        mm.z = fmaf(kp.b1, mm.z, ob1 * g.z); vv.z = fmaf(kp.b2, vv.z, ob2 * g.z * g.z);
+        mm.w = fmaf(kp.b1, mm.w, ob1 * g.w); vv.w = fmaf(kp.b2, vv.w, ob2 * g.w * g.w);
+        float4 cn;
+        cn.x = c.x - lr_t * mm.x / fmaf(sqrtf(vv.x), isb2, kp.eps);
+        cn.y = c.y - lr_t * mm.y / fmaf(sqrtf(vv.y), isb2, kp.eps);
+        cn.z = c.z - lr_t * mm.z / fmaf(sqrtf(vv.z), isb2, kp.eps);
+        cn.w = c.w - lr_t * mm.w / fmaf(sqrtf(vv.w), isb2, kp.eps);
+        kp.adam_m[idx] = mm;
+        kp.adam_v[idx] = vv;
+        kp.ctrl_w[idx] = cn;
+    }
+}
+
+// The only tile of its item, with A kept in shared memory: the net block holds,
+// for each control row, the first covering unit's block, and the overflow block
+// of unit u (pb rows from its first row) its share of rows an earlier unit also
+// covers.  s_units[3u..3u+2] = first control row, row count and the last control
+// row of the earlier units; columns [jlo, jlo+cw) were written.  Units are added
+// in order and every control point is finished.
+static __device__ __noinline__ void final_ctrl_smem(const KParams& kp, int item, int nwr, int pb,
+                                                    const int* s_units, int jlo, int cw)
+{
+    extern __shared__ float4 smem4[];
+    unsigned char* smem = reinterpret_cast<unsigned char*>(smem4);
+    const ItemDev it = kp.items[item];
+    if (kp.grad_ctrl == nullptr && !kp.fit) return;
+    const int m1 = it.m1, ncp = it.n1 * m1;
+    const float4* sB = reinterpret_cast<const float4*>(smem + kp.off_sa);
+    const float4* sO = sB + ncp;
+    float lr_t, isb2;
+    adam_corrections(kp, it, lr_t, isb2);
+    for (int e = threadIdx.x; e < ncp; e += blockDim.x) {
+        const int i = e / m1, j = e - i * m1;
+        float4 a = f4zero();
+        if (j >= jlo && j < jlo + cw) {
+            bool cov = false;
+            for (int u = 0; u < nwr; ++u) {
+                const int ilo = s_units[3 * u], nr = s_units[3 * u + 1];
+                cov |= nr > 0 && i >= ilo && i < ilo + nr;
+            }
+            if (cov) a = sB[e];
+            for (int u = 1; u < nwr; ++u) {
+                const int ilo = s_units[3 * u], nr = s_units[3 * u + 1], pm = s_units[3 * u + 2];
+                if (nr > 0 && i >= ilo && i < ilo + nr && i <= pm) {
+                    const float4 v = sO[(u * pb + i - ilo) * m1 + j];
+                    a.x += v.x; a.y += v.y; a.z += v.z; a.w += v.w;
+                }
+            }
+        }
+        finish_ctrl(kp, it, e, a, lr_t, isb2);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Final, fixed-order reduction of one item's partials (run by the last CTA to
 // finish a tile of the item): loss, knot gradients, control-point gradients
 // (homogeneous adjoint -> Cartesian P and w), and the optional Adam update.
 // ---------------------------------------------------------------------------
-static __device__ __noinline__ void final_reduce(const KParams& kp, int item)
+static __device__ __noinline__ void final_reduce(const KParams& kp, int item, bool ctrl_only)
 {
     extern __shared__ float4 smem4[];
     unsigned char* smem = reinterpret_cast<unsigned char*>(smem4);
@@ -200,12 +281,12 @@ static __device__ __noinline__ void final_reduce(const KParams& kp, int item)
     const int tid = threadIdx.x, bs = blockDim.x;
     const TileDev* T = kp.tiles + it.first_tile;
 
-    if (kp.loss_items != nullptr && tid == 0) {
+    if (!ctrl_only && kp.loss_items != nullptr && tid == 0) {
         float L = 0.f;
         for (int t = 0; t < it.ntiles; ++t) L += __ldcg(tile_slot(kp, T[t]) + 8);
         kp.loss_items[item] = L;
     }
-    if (kp.grad_knots != nullptr) {
+    if (!ctrl_only && kp.grad_knots != nullptr) {
         if (!it.curve) {
             const int nU = it.n1 + it.p + 1;
             for (int K = tid; K < nU; K += bs) {
@@ -259,36 +340,9 @@ static __device__ __noinline__ void final_reduce(const KParams& kp, int item)
     }
     __syncthreads();
     const int m1 = it.m1, ncp = it.n1 * m1;
-    // Adam bias corrections: the launch's, or this item's own step
-    float lr_t = kp.lr_t, isb2 = kp.inv_sqrt_bc2;
-    if (kp.fit && it.adam_step > 0 && it.adam_step != kp.step) {
-        const float t = (float)it.adam_step;
-        lr_t = kp.lr / (1.f - powf(kp.b1, t));
-        isb2 = rsqrtf(1.f - powf(kp.b2, t));
-    }
-    auto finish = [&](int e, float4 a) {
-        const long long idx = it.ctrl + e;
-        const float4 c = kp.ctrl[idx];
-        // Pw = (w x, w y, w z, w): dL/dx = w A.x, ..., dL/dw = x A.x + y A.y + z A.z + A.w
-        const float4 g = make_float4(c.w * a.x, c.w * a.y, c.w * a.z, fmaf(c.x, a.x, fmaf(c.y, a.y, fmaf(c.z, a.z, a.w))));
-        if (kp.grad_ctrl != nullptr) kp.grad_ctrl[idx] = g;
-        if (kp.fit) {
-            float4 mm = kp.adam_m[idx], vv = kp.adam_v[idx];
-            const float ob1 = 1.f - kp.b1, ob2 = 1.f - kp.b2;
-            mm.x = fmaf(kp.b1, mm.x, ob1 * g.x); vv.x = fmaf(kp.b2, vv.x, ob2 * g.x * g.x);
-            mm.y = fmaf(kp.b1, mm.y, ob1 * g.y); vv.y = fmaf(kp.b2, vv.y, ob2 * g.y * g.y);
-            mm.z = fmaf(kp.b1, mm.z, ob1 * g.z); vv.z = fmaf(kp.b2, vv.z, ob2 * g.z * g.z);
-            mm.w = fmaf(kp.b1, mm.w, ob1 * g.w); vv.w = fmaf(kp.b2, vv.w, ob2 * g.w * g.w);
-            float4 cn;
-            cn.x = c.x - lr_t * mm.x / fmaf(sqrtf(vv.x), isb2, kp.eps);
-            cn.y = c.y - lr_t * mm.y / fmaf(sqrtf(vv.y), isb2, kp.eps);
-            cn.z = c.z - lr_t * mm.z / fmaf(sqrtf(vv.z), isb2, kp.eps);
-            cn.w = c.w - lr_t * mm.w / fmaf(sqrtf(vv.w), isb2, kp.eps);
-            kp.adam_m[idx] = mm;
-            kp.adam_v[idx] = vv;
-            kp.ctrl_w[idx] = cn;
-        }
-    };
+    float lr_t, isb2;
+    adam_corrections(kp, it, lr_t, isb2);
+    auto finish = [&](int e, float4 a) { finish_ctrl(kp, it, e, a, lr_t, isb2); };
     // two control points per pass; the loads of four units for both are issued
     // before any is summed, and the sums run in unit order
     constexpr int UB = 4;
@@ -339,6 +393,9 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
     extern __shared__ float4 smem4[];
     unsigned char* smem = reinterpret_cast<unsigned char*>(smem4);
     constexpr int PB = P + 1, QB = Q + 1;
+    // shared-table strides: basis rows padded to float4 loads, knot windows exact
+    constexpr int SU = (PB + 3) & ~3, SV = (QB + 3) & ~3;
+    constexpr int KU = 2 * P > 0 ? 2 * P : 1, KV = 2 * Q;
     const TileDev tl = kp.tiles[t];
     const ItemDev it = kp.items[tl.item];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, bs = blockDim.x;
@@ -476,7 +533,7 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
         s_su[r] = s;
         s_u[r] = u0;
 #pragma unroll
-        for (int k = 0; k < PB; ++k) s_nu[r * kMaxBasis + k] = N[k];
+        for (int k = 0; k < PB; ++k) s_nu[r * SU + k] = N[k];
     }
     // ---- column prologue: span and v-basis per sample column
     for (int c = tid; c < npro_c; c += bs) {
@@ -487,7 +544,7 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
         s_sv[c] = s;
         s_v[c] = v0;
 #pragma unroll
-        for (int k = 0; k < QB; ++k) s_nv[c * kMaxBasis + k] = N[k];
+        for (int k = 0; k < QB; ++k) s_nv[c * SV + k] = N[k];
     }
     __syncthreads();
     // ---- the sliding windows need non-decreasing spans; anything else is refused.
@@ -552,7 +609,7 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
             float* w = s_w + s_joff[jj];
             for (int q = 0; q < r2.y; ++q) {
                 const int b = r2.x + q;
-                w[q] = s_nv[b * kMaxBasis + (j - s_sv[b] + Q)];
+                w[q] = s_nv[b * SV + (j - s_sv[b] + Q)];
             }
         }
     }
@@ -582,7 +639,7 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
         const float vb = s_v[blc];
         float Nv[QB];
 #pragma unroll
-        for (int h = 0; h < QB; ++h) Nv[h] = s_nv[blc * kMaxBasis + h];
+        for (int h = 0; h < QB; ++h) Nv[h] = s_nv[blc * SV + h];
         const float4* __restrict__ cbase = kp.ctrl + it.ctrl + (svb - Q);  // column of h = 0
         const int m1 = it.m1;
 
@@ -611,6 +668,15 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
         // Retired control rows (consecutive, from ilo) wait in tbuf until kBatch of
         // them are contracted together over the tile columns by the whole unit.
         float4* tbuf = reinterpret_cast<float4*>(smem + kp.off_stage) + wr * (kBatch * uthreads);
+        // single-tile items whose A fits keep it in shared memory (dense rows by control
+        // index, one block per unit); others write dense rows from ilo to the unit slot
+        // Rows a unit shares with an earlier unit (at most P+1, those up to pm, the last
+        // control row of the sample rows before the unit's) go to the unit's overflow
+        // block; every other row has a single first writer in the shared net block.
+        const bool sa = GRAD && it.smemA;
+        const int pm = wr > 0 ? s_su[ra - 1] : -1;
+        float4* sA = reinterpret_cast<float4*>(smem + kp.off_sa) + jlo_t;
+        float4* sOv = sA + (it.n1 + wr * PB) * it.m1;
         float4* uA = GRAD ? reinterpret_cast<float4*>(uslot + it.abase) : nullptr;
         int nb = 0, nst = 0, ilo = -1;
         auto flush = [&]() {
@@ -636,9 +702,12 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
                     const int lo = lower_bound_i(s_sv, ncols, j), hi = lower_bound_i(s_sv, ncols, j + Q + 1);
                     const float4* tb = tbuf + k * uthreads;
                     acc = f4zero();
-                    for (int b = lo; b < hi; ++b) acc = fma4(s_nv[b * kMaxBasis + (j - s_sv[b] + Q)], tb[b], acc);
+                    for (int b = lo; b < hi; ++b) acc = fma4(s_nv[b * SV + (j - s_sv[b] + Q)], tb[b], acc);
                 }
-                uA[(nst + k) * m1 + jj] = acc;
+                const int gi = ilo + nst + k;
+                if (!sa) uA[(nst + k) * m1 + jj] = acc;
+                else if (gi <= pm) sOv[(gi - ilo) * m1 + jj] = acc;
+                else sA[gi * m1 + jj] = acc;
             }
             nst += nb;
             nb = 0;
@@ -695,7 +764,7 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
         const int rstride = 3 * it.nv;                        // floats between sample rows
         const bool store = cvalid && kp.pts != nullptr;
         float* orow = kp.pts != nullptr ? kp.pts + 3 * (prow0 + lane) : nullptr;   // row 0 of this lane
-        float* s_beta_w = reinterpret_cast<float*>(smem + kp.off_beta) + (wc * kp.R) * kMaxBasis;
+        float* s_beta_w = reinterpret_cast<float*>(smem + kp.off_beta) + (wc * kp.R) * SU;
 
         // One or two rows (same u-span) per step: S, dL/dS, lambda, tau and beta.
         // NR = rows in the step; the ring slots of rows < r are free for refills.
@@ -706,7 +775,7 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
             }
             float Nu[NR][PB];
 #pragma unroll
-            for (int q = 0; q < NR; ++q) load_basis<PB>(s_nu + (r + q) * kMaxBasis, Nu[q]);
+            for (int q = 0; q < NR; ++q) load_basis<PB>(s_nu + (r + q) * SU, Nu[q]);
             // homogeneous point and perspective divide (Sec. 3.1 step 3)
             float Sx[NR], Sy[NR], Sz[NR], inv[NR];
 #pragma unroll
@@ -763,7 +832,7 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
                     const int idx = reduce_index<VB>(lane);
                     if ((lane & (32 / VB - 1)) == 0 && idx < NR * PB) {
                         const int q = idx / PB;
-                        s_beta_w[(r + q) * kMaxBasis + (idx - q * PB)] = beta[0];
+                        s_beta_w[(r + q) * SU + (idx - q * PB)] = beta[0];
                     }
                 }
             }
@@ -783,22 +852,34 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
             for (int k = 0; k < PB; ++k) retire(cur - P + k, tau[k]);
             if (nb > 0) flush();
             if (ut == 0) {
-                int* uh = reinterpret_cast<int*>(uslot);
-                uh[0] = ilo; uh[1] = nst; uh[2] = jlo_t; uh[3] = cw_t; uh[4] = 1;
+                if (sa) {
+                    s_flag[32 + 3 * wr] = ilo;
+                    s_flag[33 + 3 * wr] = nst;
+                    s_flag[34 + 3 * wr] = pm;
+                } else {
+                    int* uh = reinterpret_cast<int*>(uslot);
+                    uh[0] = ilo; uh[1] = nst; uh[2] = jlo_t; uh[3] = cw_t; uh[4] = 1;
+                }
             }
             if constexpr (KNOTS) {
                 if (cvalid) {
                     float dk[2 * Q + 1];
                     basis_knot_vjp<Q>(svb, vb, s_knV, Gam, dk);
-                    float* dv = reinterpret_cast<float*>(smem + kp.off_dvc) + (wr * kp.C + bl) * kMaxKnotWin;
+                    float* dv = reinterpret_cast<float*>(smem + kp.off_dvc) + (wr * kp.C + bl) * KV;
 #pragma unroll
                     for (int k = 0; k < 2 * Q; ++k) dv[k] = dk[k];
                 }
             }
         }
     } else if (GRAD && wr < nwr && wc == 0 && lane == 0) {
-        int* uh = reinterpret_cast<int*>(uslot);
-        uh[0] = 0; uh[1] = 0; uh[2] = 0; uh[3] = 0; uh[4] = 0;
+        if (it.smemA) {
+            s_flag[32 + 3 * wr] = 0;
+            s_flag[33 + 3 * wr] = 0;
+            s_flag[34 + 3 * wr] = -1;
+        } else {
+            int* uh = reinterpret_cast<int*>(uslot);
+            uh[0] = 0; uh[1] = 0; uh[2] = 0; uh[3] = 0; uh[4] = 0;
+        }
     }
 
     if constexpr (GRAD) {
@@ -808,11 +889,20 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
         if (lane == 0) s_red[warp] = lossacc;
         __syncthreads();
         int* sh = reinterpret_cast<int*>(slot);
+        const bool single = it.ntiles == 1;   // this CTA finishes the item itself
         if (tid == 0) {
             float L = 0.f;
             for (int w = 0; w < (bs >> 5); ++w) L += s_red[w];
             slot[8] = L;
             sh[4] = bad ? 0 : 1;
+            if (single && kp.loss_items != nullptr) kp.loss_items[tl.item] = L;
+        }
+        // single-tile items: final knot gradients straight from the gathers below
+        // (knots outside the tile's windows and the p+1 end knots get 0)
+        if (single && kp.grad_knots != nullptr && (!KNOTS || bad)) {
+            if constexpr (P > 0)
+                for (int K = tid; K < it.n1 + P + 1; K += bs) kp.grad_knots[it.knot_u + K] = 0.f;
+            for (int K = tid; K < it.m1 + Q + 1; K += bs) kp.grad_knots[it.knot_v + K] = 0.f;
         }
         if constexpr (KNOTS) {
             if (!bad) {
@@ -829,14 +919,14 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
                         for (int k = 0; k < PB; ++k) bsum[k] = 0.f;
                         for (int w = 0; w < nwc_valid; ++w) {
                             float bw[PB];
-                            load_basis<PB>(s_beta + (w * kp.R + r) * kMaxBasis, bw);
+                            load_basis<PB>(s_beta + (w * kp.R + r) * SU, bw);
 #pragma unroll
                             for (int k = 0; k < PB; ++k) bsum[k] += bw[k];
                         }
                         float dk[2 * P + 1];
                         basis_knot_vjp<P>(s_su[r], s_u[r], s_knU, bsum, dk);
 #pragma unroll
-                        for (int k = 0; k < 2 * P; ++k) s_duc[r * kMaxKnotWin + k] = dk[k];
+                        for (int k = 0; k < 2 * P; ++k) s_duc[r * KU + k] = dk[k];
                     }
                 }
                 __syncthreads();
@@ -846,8 +936,8 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
                         const int r = e / (2 * P), k = e - r * (2 * P);
                         if (r > 0 && s_su[r - 1] == s_su[r]) continue;   // not a run start
                         float acc = 0.f;
-                        for (int q = r; q < s_run[r]; ++q) acc += s_duc[q * kMaxKnotWin + k];
-                        s_duc[r * kMaxKnotWin + k] = acc;
+                        for (int q = r; q < s_run[r]; ++q) acc += s_duc[q * KU + k];
+                        s_duc[r * KU + k] = acc;
                     }
                 }
                 for (int e = tid; e < ncols * 2 * Q; e += bs) {
@@ -856,20 +946,30 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
                     float acc = 0.f;
                     for (int g = 0; g < nwr; ++g) {
                         if (g * rpg >= nrows) break;
-                        for (int q = c; q < s_crun[c]; ++q) acc += s_dvc[(g * kp.C + q) * kMaxKnotWin + k];
+                        for (int q = c; q < s_crun[c]; ++q) acc += s_dvc[(g * kp.C + q) * KV + k];
                     }
-                    s_dvc[c * kMaxKnotWin + k] = acc;   // row group 0's slot holds the run sum
+                    s_dvc[c * KV + k] = acc;   // row group 0's slot holds the run sum
                 }
                 __syncthreads();
                 if constexpr (P > 0) {
                     const int ku_lo = s_su[0] - P + 1;
                     const int nku = s_su[nrows - 1] + P - ku_lo + 1;
-                    for (int K = tid; K < nku; K += bs) {
-                        const int kk = ku_lo + K;
-                        float acc = 0.f;
-                        for (int r = lower_bound_i(s_su, nrows, kk - P); r < nrows && s_su[r] <= kk + P - 1; r = s_run[r])
-                            acc += s_duc[r * kMaxKnotWin + (kk - (s_su[r] - P + 1))];
-                        slot[12 + K] = acc;
+                    if (single) {
+                        for (int kk = tid; kk < it.n1 + P + 1; kk += bs) {
+                            float acc = 0.f;
+                            if (kk >= P + 1 && kk <= it.n1 - 1 && kk >= ku_lo && kk < ku_lo + nku)
+                                for (int r = lower_bound_i(s_su, nrows, kk - P); r < nrows && s_su[r] <= kk + P - 1; r = s_run[r])
+                                    acc += s_duc[r * KU + (kk - (s_su[r] - P + 1))];
+                            kp.grad_knots[it.knot_u + kk] = acc;
+                        }
+                    } else {
+                        for (int K = tid; K < nku; K += bs) {
+                            const int kk = ku_lo + K;
+                            float acc = 0.f;
+                            for (int r = lower_bound_i(s_su, nrows, kk - P); r < nrows && s_su[r] <= kk + P - 1; r = s_run[r])
+                                acc += s_duc[r * KU + (kk - (s_su[r] - P + 1))];
+                            slot[12 + K] = acc;
+                        }
                     }
                     if (tid == 0) { sh[0] = ku_lo; sh[1] = nku; }
                 } else {
@@ -877,12 +977,22 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
                 }
                 const int kv_lo = s_sv[0] - Q + 1;
                 const int nkv = s_sv[ncols - 1] + Q - kv_lo + 1;
-                for (int K = tid; K < nkv; K += bs) {
-                    const int kk = kv_lo + K;
-                    float acc = 0.f;
-                    for (int c = lower_bound_i(s_sv, ncols, kk - Q); c < ncols && s_sv[c] <= kk + Q - 1; c = s_crun[c])
-                        acc += s_dvc[c * kMaxKnotWin + (kk - (s_sv[c] - Q + 1))];
-                    slot[12 + it.ku_cap + K] = acc;
+                if (single) {
+                    for (int kk = tid; kk < it.m1 + Q + 1; kk += bs) {
+                        float acc = 0.f;
+                        if (kk >= Q + 1 && kk <= it.m1 - 1 && kk >= kv_lo && kk < kv_lo + nkv)
+                            for (int c = lower_bound_i(s_sv, ncols, kk - Q); c < ncols && s_sv[c] <= kk + Q - 1; c = s_crun[c])
+                                acc += s_dvc[c * KV + (kk - (s_sv[c] - Q + 1))];
+                        kp.grad_knots[it.knot_v + kk] = acc;
+                    }
+                } else {
+                    for (int K = tid; K < nkv; K += bs) {
+                        const int kk = kv_lo + K;
+                        float acc = 0.f;
+                        for (int c = lower_bound_i(s_sv, ncols, kk - Q); c < ncols && s_sv[c] <= kk + Q - 1; c = s_crun[c])
+                            acc += s_dvc[c * KV + (kk - (s_sv[c] - Q + 1))];
+                        slot[12 + it.ku_cap + K] = acc;
+                    }
                 }
                 if (tid == 0) { sh[2] = kv_lo; sh[3] = nkv; }
             } else if (tid == 0) {
@@ -891,19 +1001,26 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
         } else if (tid == 0) {
             sh[0] = 0; sh[1] = 0; sh[2] = 0; sh[3] = 0;
         }
-        // publish the partials (the barrier orders the CTA's writes before thread 0's
-        // device-scope fence); the last tile of the item reduces them
-        __syncthreads();
-        if (tid == 0) {
-            __threadfence();
-            const unsigned prev = atomicAdd(kp.counts + tl.item, 1u);
-            s_flag[1] = (prev + 1 == (unsigned)it.ntiles) ? 1 : 0;
-        }
-        __syncthreads();
-        if (s_flag[1]) {
-            __threadfence();
-            final_reduce(kp, tl.item);
-            if (tid == 0) kp.counts[tl.item] = 0u;
+        if (single) {
+            // the only tile of its item: reduce its own units (shared memory or its slot)
+            __syncthreads();
+            if (it.smemA) final_ctrl_smem(kp, tl.item, nwr, PB, s_flag + 32, jlo_t, cw_t);
+            else final_reduce(kp, tl.item, true);
+        } else {
+            // publish the partials (the barrier orders the CTA's writes before thread 0's
+            // device-scope fence); the last tile of the item reduces them
+            __syncthreads();
+            if (tid == 0) {
+                __threadfence();
+                const unsigned prev = atomicAdd(kp.counts + tl.item, 1u);
+                s_flag[1] = (prev + 1 == (unsigned)it.ntiles) ? 1 : 0;
+            }
+            __syncthreads();
+            if (s_flag[1]) {
+                __threadfence();
+                final_reduce(kp, tl.item, false);
+                if (tid == 0) kp.counts[tl.item] = 0u;
+            }
         }
     }
     cp_async_wait<0>();

@@ -14,7 +14,7 @@ import torch
 
 from . import batch
 
-DEFAULT_CANDIDATES = [(4, 16), (4, 32), (4, 64), (8, 32), (8, 64), (8, 128), (2, 16), (2, 32)]
+DEFAULT_CANDIDATES = [(8, 32), (8, 64), (8, 128), (4, 32), (4, 64), (4, 128), (2, 32)]
 _cache: dict = {}
 
 

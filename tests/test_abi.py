@@ -70,7 +70,7 @@ def test_planner_rejects_bad_descriptors():
     assert _plan(7, pk.descs)[0] == 1                    # kind
     cfg = _lib.TileCfg(0, 9, 0, 0)                       # more warps than the kernels allow
     assert _plan(_lib.KIND_SURFACE, pk.descs, cfg)[0] == 1
-    cfg = _lib.TileCfg(0, 4, 0, -1)                      # negative CTA cap
+    cfg = _lib.TileCfg(0, 8, 0, -1)                      # negative CTA cap
     assert _plan(_lib.KIND_SURFACE, pk.descs, cfg)[0] == 1
 
 

@@ -46,7 +46,7 @@ def test_forward_mixed_degrees_ragged():
     check_points(surfs, SURF, got)
 
 
-@pytest.mark.parametrize("warps,rows", [(1, 0), (2, 5), (4, 0), (8, 3), (8, 64)])
+@pytest.mark.parametrize("warps,rows", [(1, 0), (2, 5), (4, 0), (4, 3), (4, 64), (8, 0), (8, 128), (8, 9)])
 def test_forward_tile_shapes(warps, rows):
     surfs = mixed_surfaces(2, 6)
     _, got = gpu_eval(surfs, SURF, warps=warps, rows=rows)
@@ -142,7 +142,7 @@ def test_backward_without_knots_matches():
     _check_grads(items, SURF, pk, g, gc, None)
 
 
-@pytest.mark.parametrize("warps,rows", [(1, 0), (2, 7), (8, 2), (4, 100)])
+@pytest.mark.parametrize("warps,rows", [(1, 0), (2, 7), (4, 2), (4, 100), (8, 0), (8, 64), (8, 200), (6, 50)])
 def test_backward_tile_shapes(warps, rows):
     items = mixed_surfaces(7, 6)
     pk, g, gc, gk = _run_backward(items, SURF, 7, warps=warps, rows=rows)
