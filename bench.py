@@ -52,6 +52,32 @@ def algorithmic_bytes(npts: int, descs) -> int:
     return b
 
 
+KERNEL_SOURCES = ("nurbs_tile.cuh", "nurbs_kernel.cuh", "nurbs_basis.cuh", "nurbs_tables.h")
+
+
+def kernel_sources_sha1() -> str:
+    import hashlib
+    h = hashlib.sha1()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2104_14547_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def measured_traffic(tile: str):
+    """DRAM bytes (read + write) per launch of the step's kernel from the committed
+    ncu capture, or None when the kernel sources or the tile shape differ from
+    the ones the counters were taken on."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+            rec = json.load(fh)["tiles_kernel_mse_knots_bicubic256"]
+    except (OSError, KeyError, ValueError):
+        return None
+    if rec.get("kernel_sources_sha1") != kernel_sources_sha1() or rec.get("tile") != tile:
+        return None
+    return rec.get("bytes_per_launch")
+
+
 class ClockSampler:
     """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
 
@@ -143,9 +169,12 @@ def run_ours(args):
     gc = torch.empty_like(ct)
     gk = torch.empty_like(kn)
     loss = torch.empty(pk.count, device=dev)
-    # tile shape from the autotuner (untimed), then the plan the step runs
-    best, table = tune.autotune(pk, dict(knots=kn, ctrl=ct, params=pr, target=target, pts=pts, grad_ctrl=gc,
-                                         grad_knots=gk, loss=loss), op="mse", device=dev)
+    # tile shape from the autotuner (untimed) unless given, then the plan the step runs
+    if args.tile:
+        best, table = tuple(int(x) for x in args.tile.split(",")), {}
+    else:
+        best, table = tune.autotune(pk, dict(knots=kn, ctrl=ct, params=pr, target=target, pts=pts, grad_ctrl=gc,
+                                             grad_knots=gk, loss=loss), op="mse", device=dev)
     plan = batch.Plan.for_packed(pk, device=dev, warps=best[0], rows=best[1])
     scale = 2.0 / (3.0 * npts)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)   # > L2 (129 MB)
@@ -192,12 +221,7 @@ def run_ours(args):
     except Exception:
         pass
     peak = float(peaks.get("hbm_gbs", 6800.0))
-    traffic = None
-    try:
-        prof = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
-        traffic = prof.get("fused_mse_fwd_bwd_cfg2_bytes_per_launch")
-    except Exception:
-        pass
+    traffic = measured_traffic(f"w{best[0]}r{best[1]}")
 
     # end to end through the public API: pinned host inputs in, loss + gradients out
     h_target = target.cpu().pin_memory()
@@ -465,6 +489,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-extra", action="store_true", help="skip the curve and ragged workloads")
+    ap.add_argument("--tile", default="", help="fixed tile shape 'warps,rows' instead of the autotuner's")
     ap.add_argument("--serve", action="store_true", help="also run the serving sweep (Poisson arrivals)")
     ap.add_argument("--serve-requests", type=int, default=20000)
     args = ap.parse_args()
