@@ -133,11 +133,11 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def make_workload(device):
+def make_workload(device, seed: int = 0):
     import torch
 
     from paper_2104_14547_gb300 import batch, synth
-    surfs, targets = synth.bicubic_batch(0, WORKLOAD["batch"], WORKLOAD["net"], WORKLOAD["grid"])
+    surfs, targets = synth.bicubic_batch(seed, WORKLOAD["batch"], WORKLOAD["net"], WORKLOAD["grid"])
     pk = batch.pack_surfaces(surfs)
     tk = batch.pack_surfaces(targets)
     kn, ct, pr = batch.to_device(pk, device)
@@ -152,18 +152,19 @@ def make_workload(device):
 
 def run_ours(args):
     import torch
-    import torch.distributed as dist
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        dist.init_process_group("nccl")
+    from paper_2104_14547_gb300 import replicas
+
+    # one process per GPU, each with its own seeded shard of independent surfaces
+    rk = replicas.init("nccl")
+    world, rank, local = rk.world, rk.rank, rk.local
+    if world != args.gpus:
+        raise SystemExit(f"--gpus {args.gpus} but {world} rank(s): launch N > 1 under torch.distributed.run")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     from paper_2104_14547_gb300 import batch, tune
 
-    pk, kn, ct, pr, target = make_workload(dev)
+    pk, kn, ct, pr, target = make_workload(dev, replicas.shard_seed(0, rank))
     npts = pk.npts
     pts = torch.empty((npts, 3), device=dev)
     gc = torch.empty_like(ct)
@@ -191,8 +192,7 @@ def run_ours(args):
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     clocks = ClockSampler(local)
-    if world > 1:
-        dist.barrier()
+    replicas.barrier()
     torch.cuda.synchronize(dev)
     clocks.start()
     for k in range(args.steps):
@@ -203,14 +203,10 @@ def run_ours(args):
     torch.cuda.synchronize(dev)
     clk = clocks.stop()
     ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    t_ms = float(np.sum(ms))
-    if world > 1:
-        tt = torch.tensor([t_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        dist.barrier()
-        t_ms = float(tt.item())
+    value = replicas.job_rate(npts * args.steps, float(np.sum(ms)) / 1e3, dev)
+    t_ms = replicas.max_over_ranks(float(np.sum(ms)), dev)
+    replicas.barrier()
     ms_per_step = t_ms / args.steps
-    value = world * npts * args.steps / (t_ms / 1e3)
 
     # roofline of the one kernel of the step (the fused forward+backward tile kernel)
     abytes = algorithmic_bytes(npts, pk.descs)
@@ -257,11 +253,7 @@ def run_ours(args):
         e1.record(stream)
         e1.synchronize()
         e_ms += e0.elapsed_time(e1)
-    if world > 1:
-        tt = torch.tensor([e_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e_ms = float(tt.item())
-    e2e_value = world * npts * args.steps / (e_ms / 1e3)
+    e2e_value = replicas.job_rate(npts * args.steps, e_ms / 1e3, dev)
 
     extras = {}
     if rank == 0 and not args.no_extra:
@@ -295,8 +287,7 @@ def run_ours(args):
         if extras:
             line["extra"] = extras
         print(json.dumps(line), flush=True)
-    if world > 1:
-        dist.destroy_process_group()
+    replicas.finalize()
 
 
 def cpu_baseline(budget_s: float = 15.0):
