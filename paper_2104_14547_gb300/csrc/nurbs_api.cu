@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "../../include/nurbs.h"
+#include "nurbs_curve.cuh"
 #include "nurbs_kernel.cuh"
 
 using namespace nurbs;
@@ -37,6 +38,7 @@ nurbs_status cuda_fail(cudaError_t e)
 
 struct PlanGroup {
     int p, q;         // internal degrees (p == 0 for curves)
+    int ck;           // 1: curve-kernel group (degree q, one warp per curve)
     int t0, t1;       // tile range
     int grid[5];      // CTAs per launch of each kernel variant (0 = unknown)
 };
@@ -52,9 +54,10 @@ struct nurbs_plan {
     // shared memory carve-up
     int R, C, acc_cap;
     int off_misc, off_su, off_u, off_nu, off_sv, off_v, off_nv, off_stage, off_beta, off_duc, off_dvc, off_ring,
-        off_jb, off_win, off_run, off_crun, off_knots, off_w, off_acc, off_sa;
+        off_jb, off_win, off_run, off_knots, off_w, off_acc, off_sa;
     int smem_bytes;           // gradient kernels
     int smem_eval;            // forward kernels (no shared adjoint)
+    int c_mc, c_wbytes, c_smem;   // curve kernels: control capacity, bytes per warp, per CTA
     // workspace layout (bytes)
     size_t items_off, tiles_off, counts_off, part_off, ws_bytes;
     // binding
@@ -143,16 +146,48 @@ nurbs_status nurbs_plan_create(int32_t kind, const nurbs_desc* h_desc, int32_t c
         max_m1 = std::max(max_m1, it.m1);
         pl->items.push_back(it);
     }
-    // tiles, grouped by degree pair so that each group runs one specialised kernel
-    for (int g = 0; g < kMaxGroups; ++g) {
-        const int gp = g / 5, gq = g % 5 + 1;
+    // curves with at most kCurveCtrlCap control points run on the curve kernels:
+    // one tile (one warp) per curve, one group per degree
+    pl->c_mc = 4;
+    pl->c_wbytes = 0;
+    for (ItemDev& it : pl->items) {
+        it.ck = (kind == NURBS_KIND_CURVE && it.m1 <= kCurveCtrlCap) ? 1 : 0;
+        if (it.ck) pl->c_mc = std::max(pl->c_mc, it.m1);
+    }
+    for (int q = 1; q <= NURBS_MAX_DEGREE; ++q) {
         PlanGroup grp;
-        grp.p = gp; grp.q = gq;
+        grp.p = 0; grp.q = q; grp.ck = 1;
         grp.t0 = (int)pl->tiles.size();
         for (int v = 0; v < 5; ++v) grp.grid[v] = 0;
         for (int32_t k = 0; k < count; ++k) {
             ItemDev& it = pl->items[k];
-            if (it.p != gp || it.q != gq) continue;
+            if (!it.ck || it.q != q) continue;
+            it.first_tile = (int)pl->tiles.size();
+            it.ntiles = 1;
+            TileDev tl;
+            std::memset(&tl, 0, sizeof tl);
+            tl.item = k;
+            tl.nrows = it.nu;
+            tl.ncols = it.nv;
+            pl->tiles.push_back(tl);
+        }
+        grp.t1 = (int)pl->tiles.size();
+        if (grp.t1 > grp.t0) {
+            pl->groups.push_back(grp);
+            pl->c_wbytes = std::max(pl->c_wbytes, curve_warp_bytes(pl->c_mc, q));
+        }
+    }
+    pl->c_smem = kCurveWarps * pl->c_wbytes;
+    // tiles, grouped by degree pair so that each group runs one specialised kernel
+    for (int g = 0; g < kMaxGroups; ++g) {
+        const int gp = g / 5, gq = g % 5 + 1;
+        PlanGroup grp;
+        grp.p = gp; grp.q = gq; grp.ck = 0;
+        grp.t0 = (int)pl->tiles.size();
+        for (int v = 0; v < 5; ++v) grp.grid[v] = 0;
+        for (int32_t k = 0; k < count; ++k) {
+            ItemDev& it = pl->items[k];
+            if (it.p != gp || it.q != gq || it.ck) continue;
             it.first_tile = (int)pl->tiles.size();
             // column tiles of at most 32*NW samples; row tiles of R rows split into row groups
             const int nct = std::max(1, (it.nv + maxcols - 1) / maxcols);
@@ -231,7 +266,6 @@ nurbs_status nurbs_plan_create(int32_t kind, const nurbs_desc* h_desc, int32_t c
     pl->off_jb = take(8 * kJbCap);
     pl->off_win = take(16 * kWinCap);
     pl->off_run = take(4 * maxR);
-    pl->off_crun = take(4 * maxC);
     int max_knots = 4;
     for (const ItemDev& it : pl->items)
         max_knots = std::max(max_knots, align4(it.n1 + it.p + 1) + it.m1 + it.q + 1);
@@ -320,15 +354,50 @@ KernelVariant variant_for(int v, int p, int q)
     }
 }
 
-// Launch variant v (0 forward, 1/2 backward from dL/dS without/with knots, 3/4 the
-// same from an MSE target): one persistent
-// kernel per degree group, in group order on `s`.
-nurbs_status launch(const nurbs_plan* cpl, int v, KParams& kp, cudaStream_t s)
+// Kernel, block, shared memory and queue slot of one group for variant v.
+struct GroupLaunch {
+    KernelVariant kv;
+    int block, smem, qslot, units;   // units: tiles per CTA slot (curve kernels: warps)
+};
+
+GroupLaunch group_launch(const nurbs_plan* pl, const PlanGroup& grp, int v)
 {
-    nurbs_plan* pl = const_cast<nurbs_plan*>(cpl);
-    if (pl->ws == nullptr) return NURBS_ERR_WORKSPACE;
-    if (pl->tiles.empty()) return NURBS_OK;
-    unsigned char* ws = static_cast<unsigned char*>(pl->ws);
+    if (grp.ck)
+        return GroupLaunch{curve_variant(v, grp.q), 32 * kCurveWarps, pl->c_smem, kMaxGroups + grp.q - 1, kCurveWarps};
+    return GroupLaunch{variant_for(v, grp.p, grp.q), 32 * pl->warps, v == 0 ? pl->smem_eval : pl->smem_bytes,
+                       grp.p * 5 + grp.q - 1, 1};
+}
+
+// Grid of a group for variant v (once per plan): as many persistent CTAs as fit,
+// no more than its tiles need, capped by max_ctas when `cap`.
+nurbs_status size_group(nurbs_plan* pl, PlanGroup& grp, int v, const GroupLaunch& gl, bool cap)
+{
+    if (grp.grid[v] != 0) return NURBS_OK;
+    // the attribute is per kernel function: raise it to the device limit so that
+    // no plan lowers it under another plan's launch size
+    cudaError_t e = cudaSuccess;
+    if (gl.smem > 48 * 1024) {
+        int limit = 0;
+        e = gl.kv.set_smem(&limit);
+        if (e == cudaSuccess && gl.smem > limit) return NURBS_ERR_SIZE;
+    }
+    if (e != cudaSuccess) return cuda_fail(e);
+    int occ = 0, dev = 0, sms = 0;
+    e = gl.kv.occupancy(&occ, gl.block, gl.smem);
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (occ < 1) return NURBS_ERR_SIZE;
+    if (pl->ctas_per_sm > 0) occ = std::min(occ, pl->ctas_per_sm);
+    const int need = (grp.t1 - grp.t0 + gl.units - 1) / gl.units;
+    grp.grid[v] = std::max(1, std::min(need, occ * sms));
+    if (cap && pl->max_ctas > 0) grp.grid[v] = std::min(grp.grid[v], pl->max_ctas);
+    return NURBS_OK;
+}
+
+// Workspace tables and shared-memory carve-up of a plan in the kernel parameters.
+void fill_tables(KParams& kp, const nurbs_plan* pl, unsigned char* ws)
+{
     kp.items = reinterpret_cast<const ItemDev*>(ws + pl->items_off);
     kp.tiles = reinterpret_cast<const TileDev*>(ws + pl->tiles_off);
     kp.hdr = reinterpret_cast<WsHeader*>(ws);
@@ -337,42 +406,38 @@ nurbs_status launch(const nurbs_plan* cpl, int v, KParams& kp, cudaStream_t s)
     kp.R = pl->R; kp.C = pl->C;
     kp.off_misc = pl->off_misc; kp.off_su = pl->off_su; kp.off_u = pl->off_u; kp.off_nu = pl->off_nu;
     kp.off_sv = pl->off_sv; kp.off_v = pl->off_v; kp.off_nv = pl->off_nv; kp.off_stage = pl->off_stage;
-    kp.off_beta = pl->off_beta; kp.off_duc = pl->off_duc; kp.off_dvc = pl->off_dvc; kp.off_ring = pl->off_ring; kp.off_jb = pl->off_jb; kp.off_win = pl->off_win; kp.off_run = pl->off_run; kp.off_crun = pl->off_crun; kp.off_knots = pl->off_knots; kp.off_w = pl->off_w; kp.off_sa = pl->off_sa;
-    kp.off_acc = pl->off_acc;
+    kp.off_beta = pl->off_beta; kp.off_duc = pl->off_duc; kp.off_dvc = pl->off_dvc; kp.off_ring = pl->off_ring;
+    kp.off_jb = pl->off_jb; kp.off_win = pl->off_win; kp.off_run = pl->off_run;
+    kp.off_knots = pl->off_knots; kp.off_w = pl->off_w; kp.off_sa = pl->off_sa; kp.off_acc = pl->off_acc;
     kp.acc_cap = pl->acc_cap;
-    const int block = 32 * pl->warps;
-    const int smem = v == 0 ? pl->smem_eval : pl->smem_bytes;
+    kp.c_mc = pl->c_mc;
+    kp.c_wbytes = pl->c_wbytes;
+}
+
+// Launch variant v (0 forward, 1/2 backward from dL/dS without/with knots, 3/4 the
+// same from an MSE target): one persistent kernel per group, in group order on `s`.
+nurbs_status launch_groups(nurbs_plan* pl, int v, KParams& kp, unsigned char* ws, cudaStream_t s, bool cap)
+{
+    fill_tables(kp, pl, ws);
     for (PlanGroup& grp : pl->groups) {
-        KernelVariant kv = variant_for(v, grp.p, grp.q);
-        if (grp.grid[v] == 0) {
-            // the attribute is per kernel function: raise it to the device limit so that
-            // no plan lowers it under another plan's launch size
-            cudaError_t e = cudaSuccess;
-            if (smem > 48 * 1024) {
-                int limit = 0;
-                e = kv.set_smem(&limit);
-                if (e == cudaSuccess && smem > limit) return NURBS_ERR_SIZE;
-            }
-            if (e != cudaSuccess) return cuda_fail(e);
-            int occ = 0;
-            e = kv.occupancy(&occ, block, smem);
-            if (e != cudaSuccess) return cuda_fail(e);
-            int dev = 0, sms = 0;
-            e = cudaGetDevice(&dev);
-            if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            if (e != cudaSuccess) return cuda_fail(e);
-            if (occ < 1) return NURBS_ERR_SIZE;
-            if (pl->ctas_per_sm > 0) occ = std::min(occ, pl->ctas_per_sm);
-            grp.grid[v] = std::max(1, std::min(grp.t1 - grp.t0, occ * sms));
-            if (pl->max_ctas > 0) grp.grid[v] = std::min(grp.grid[v], pl->max_ctas);
-        }
+        const GroupLaunch gl = group_launch(pl, grp, v);
+        nurbs_status st = size_group(pl, grp, v, gl, cap);
+        if (st != NURBS_OK) return st;
         kp.t0 = grp.t0;
         kp.t1 = grp.t1;
-        kp.queue = kp.hdr->queue + 2 * (grp.p * 5 + grp.q - 1);
-        cudaError_t e = kv.launch(kp, grp.grid[v], block, smem, s);
+        kp.queue = kp.hdr->queue + 2 * gl.qslot;
+        cudaError_t e = gl.kv.launch(kp, grp.grid[v], gl.block, gl.smem, s);
         if (e != cudaSuccess) return cuda_fail(e);
     }
     return NURBS_OK;
+}
+
+nurbs_status launch(const nurbs_plan* cpl, int v, KParams& kp, cudaStream_t s)
+{
+    nurbs_plan* pl = const_cast<nurbs_plan*>(cpl);
+    if (pl->ws == nullptr) return NURBS_ERR_WORKSPACE;
+    if (pl->tiles.empty()) return NURBS_OK;
+    return launch_groups(pl, v, kp, static_cast<unsigned char*>(pl->ws), s, true);
 }
 
 void zero_params(KParams& kp)
@@ -589,43 +654,6 @@ extern "C" nurbs_status nurbs_mse_fwd_bwd_noalloc(const nurbs_plan* cpl, const f
     kp.grad_knots = grad_knots;
     kp.loss_items = loss_items;
     kp.grad_scale = grad_scale;
-    kp.items = reinterpret_cast<const ItemDev*>(ws + pl->items_off);
-    kp.tiles = reinterpret_cast<const TileDev*>(ws + pl->tiles_off);
-    kp.hdr = reinterpret_cast<WsHeader*>(ws);
-    kp.counts = reinterpret_cast<unsigned int*>(ws + pl->counts_off);
-    kp.part = reinterpret_cast<float*>(ws + pl->part_off);
-    kp.R = pl->R; kp.C = pl->C;
-    kp.off_misc = pl->off_misc; kp.off_su = pl->off_su; kp.off_u = pl->off_u; kp.off_nu = pl->off_nu;
-    kp.off_sv = pl->off_sv; kp.off_v = pl->off_v; kp.off_nv = pl->off_nv; kp.off_stage = pl->off_stage;
-    kp.off_beta = pl->off_beta; kp.off_duc = pl->off_duc; kp.off_dvc = pl->off_dvc; kp.off_ring = pl->off_ring;
-    kp.off_jb = pl->off_jb; kp.off_win = pl->off_win; kp.off_run = pl->off_run; kp.off_crun = pl->off_crun;
-    kp.off_knots = pl->off_knots; kp.off_w = pl->off_w; kp.off_sa = pl->off_sa; kp.off_acc = pl->off_acc;
-    kp.acc_cap = pl->acc_cap;
     const int v = grad_knots != nullptr ? 4 : 3;
-    const int block = 32 * pl->warps;
-    for (PlanGroup& grp : pl->groups) {
-        KernelVariant kv = variant_for(v, grp.p, grp.q);
-        if (grp.grid[v] == 0) {
-            if (pl->smem_bytes > 48 * 1024) {
-                int limit = 0;
-                e = kv.set_smem(&limit);
-                if (e != cudaSuccess) return cuda_fail(e);
-                if (pl->smem_bytes > limit) return NURBS_ERR_SIZE;
-            }
-            int occ = 0, dev = 0, sms = 0;
-            e = kv.occupancy(&occ, block, pl->smem_bytes);
-            if (e == cudaSuccess) e = cudaGetDevice(&dev);
-            if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            if (e != cudaSuccess) return cuda_fail(e);
-            if (occ < 1) return NURBS_ERR_SIZE;
-            if (pl->ctas_per_sm > 0) occ = std::min(occ, pl->ctas_per_sm);
-            grp.grid[v] = std::max(1, std::min(grp.t1 - grp.t0, occ * sms));
-        }
-        kp.t0 = grp.t0;
-        kp.t1 = grp.t1;
-        kp.queue = kp.hdr->queue + 2 * (grp.p * 5 + grp.q - 1);
-        e = kv.launch(kp, grp.grid[v], block, pl->smem_bytes, s);
-        if (e != cudaSuccess) return cuda_fail(e);
-    }
-    return NURBS_OK;
+    return launch_groups(pl, v, kp, ws, s, false);
 }

@@ -1,0 +1,370 @@
+// Curve kernels: one warp per curve.
+//
+// A curve C(u) = sum_r N_r(u) Pw_r / W (the curve form of Eq. 3) has no second
+// direction to share work across, so the tile kernels' row/column split does
+// not fit it.  Here lane L of a warp takes the contiguous samples
+// [L*nb, (L+1)*nb) of its curve.  Samples are non-decreasing, so the lane walks
+// them with the knot span never decreasing and keeps in registers:
+//   - the window of the P+1 homogeneous control points Pw[s-P .. s];
+//   - their adjoint accumulators tau[r] = sum_b N_r(u_b) lambda_b, where
+//     lambda = (g / W, -S.g / W) and g = dL/dS (Eq. 7, Eq. 8);
+//   - with knot gradients, the 2P knot accumulators of the same span (the
+//     reverse-mode knot derivative of the basis, the sigma -> 0 reading of
+//     Sec. 3.2).
+//
+// Retiring rows.  A control point (or knot) leaves the window as the span
+// advances.  It then goes to the warp's shared block if this lane is its first
+// covering lane.  Otherwise it is one of the at most P+1 points (2P knots) this
+// lane shares with the previous lane, and it goes to the lane's overflow block.
+//
+// The final pass adds, for every point, the first lane's block entry and the
+// later lanes' overflow entries in lane order.  It then writes the Cartesian
+// gradient (and runs Adam, in a fit step), so results are deterministic.
+//
+// Parameters and dL/dS (or the MSE target) stream through a two-stage cp.async
+// ring per lane, kCurveRound samples a stage.
+#pragma once
+#include "nurbs_tile.cuh"
+
+namespace nurbs {
+
+constexpr int kCurveWarps = 4;        // curves in flight per CTA
+constexpr int kCurveRound = 4;        // samples per lane per staged round
+constexpr int kCurveCtrlCap = 256;    // control points per curve on this path (larger: tile kernels)
+
+// Per-warp shared layout (bytes) for degree P and control capacity mc:
+//   [0, 4 kc)            knots (kc = mc + P + 1 rounded up to 4)
+//   A      16 mc         adjoint block (one float4 per control point)
+//   K      4 kc          knot-derivative block
+//   lanes  512           int[4][32]: first span, last span, previous lane's last span, -
+//   Aov    512 (P+1)     [32][P+1] float4: each lane's overflow block of control points
+//   Kov    256 P         [32][2P] floats: each lane's overflow block of knots
+//   ring   4096          [2][32][4] float4: per lane one chunk of 4 parameters and three
+//                        chunks of 4 targets (x y z); lane L's chunk c sits at slot
+//                        c ^ ((L >> 1) & 3) so that the lanes' 128-bit reads of one
+//                        chunk hit 8 distinct bank groups per quarter warp
+__host__ __device__ constexpr int curve_kc(int mc, int P) { return (mc + P + 1 + 3) & ~3; }
+__host__ __device__ constexpr int curve_off_aov(int mc, int P) { return 8 * curve_kc(mc, P) + 16 * mc + 512; }
+__host__ __device__ constexpr int curve_off_ring(int mc, int P)
+{
+    return (curve_off_aov(mc, P) + 512 * (P + 1) + 256 * P + 15) & ~15;
+}
+__host__ __device__ constexpr int curve_warp_bytes(int mc, int P) { return curve_off_ring(mc, P) + 2 * 32 * 16 * 4; }
+
+template <int P, bool GRAD, bool KNOTS, bool MSE>
+__device__ __forceinline__ void curve_body(const KParams& kp, int t, unsigned char* wsm)
+{
+    constexpr int PB = P + 1;
+    constexpr int KW = 2 * P;
+    constexpr int R = kCurveRound;
+    const int lane = threadIdx.x & 31;
+    const int mc = kp.c_mc;
+    const int kc = curve_kc(mc, P);
+    float* s_kn = reinterpret_cast<float*>(wsm);
+    float4* s_A = reinterpret_cast<float4*>(wsm + 4 * kc);
+    float* s_K = reinterpret_cast<float*>(wsm + 4 * kc + 16 * mc);
+    int* s_ln = reinterpret_cast<int*>(wsm + 8 * kc + 16 * mc);
+    float4* s_Aov = reinterpret_cast<float4*>(wsm + curve_off_aov(mc, P));
+    float* s_Kov = reinterpret_cast<float*>(wsm + curve_off_aov(mc, P) + 512 * PB);
+    float* s_ring = reinterpret_cast<float*>(wsm + curve_off_ring(mc, P));
+
+    const int item = kp.tiles[t].item;
+    const ItemDev it = kp.items[item];
+    const int nc = it.m1, n = nc - 1, ns = it.nv, nk = nc + P + 1;
+    const float* __restrict__ gU = kp.knots + it.knot_v;
+    const float* __restrict__ gu = kp.params + it.param_v;
+    const float4* __restrict__ gP = kp.ctrl + it.ctrl;
+    const float* __restrict__ gt = GRAD ? kp.gin + 3 * it.pts : nullptr;
+
+    for (int k = lane; k < nk; k += 32) cp_async4(s_kn + k, gU + k);
+    cp_async_commit();
+
+    // this lane's samples [b0, b1): a whole number of rounds each (the last lane may be short)
+    const int nb = (ns + 32 * R - 1) / (32 * R) * R;
+    const int b0 = min(lane * nb, ns), b1 = min(b0 + nb, ns);
+    const bool act = b0 < b1;
+    const int rounds = nb / R;
+    const int nact = nb > 0 ? (ns + nb - 1) / nb : 0;   // active lanes form a prefix
+    const bool al16 = ((it.param_v & 3) == 0) && (!GRAD || (it.pts & 3) == 0);
+    const int swz = (lane >> 1) & 3;
+    auto issue = [&](int k) {
+        if (k < rounds) {
+            const int bb = b0 + k * R;
+            float* dst = s_ring + ((k & 1) * 32 + lane) * 16;
+            if (al16 && bb + R <= b1) {
+                cp_async16(dst + 4 * (0 ^ swz), gu + bb);
+                if constexpr (GRAD) {
+                    cp_async16(dst + 4 * (1 ^ swz), gt + 3 * bb);
+                    cp_async16(dst + 4 * (2 ^ swz), gt + 3 * bb + 4);
+                    cp_async16(dst + 4 * (3 ^ swz), gt + 3 * bb + 8);
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < R; ++j) {
+                    if (bb + j < b1) {
+                        cp_async4(dst + 4 * (0 ^ swz) + j, gu + bb + j);
+                        if constexpr (GRAD) {
+#pragma unroll
+                            for (int c = 0; c < 3; ++c) {
+                                const int w = 3 * j + c;   // target word of the round
+                                cp_async4(dst + 4 * ((1 + w / 4) ^ swz) + (w & 3), gt + 3 * (bb + j) + c);
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        cp_async_commit();
+    };
+    issue(0);
+    issue(1);
+    cp_async_wait<2>();   // the knots
+    __syncwarp();
+
+    // device checks and the spans of this lane's first and last samples
+    unsigned err = 0;
+    for (int k = lane; k < nk - 1; k += 32)
+        if (s_kn[k] > s_kn[k + 1]) err |= kErrKnots;
+    if (lane == 0 && !(s_kn[n] < s_kn[n + 1])) err |= kErrKnots;
+    const float ulo = s_kn[P], uhi = s_kn[n + 1];
+    int sf = P, sl = -1;
+    if (act) {
+        const float uf = gu[b0], ul = gu[b1 - 1];
+        sf = find_span(n, P, fminf(fmaxf(uf, ulo), uhi), s_kn);
+        sl = find_span(n, P, fminf(fmaxf(ul, ulo), uhi), s_kn);
+        if (b0 > 0 && gu[b0 - 1] > uf) err |= kErrOrder;
+    }
+    const int pm0 = __shfl_up_sync(0xffffffffu, sl, 1);
+    const int pm = lane == 0 ? -1 : pm0;    // the previous lane's last span
+    s_ln[lane] = sf;
+    s_ln[32 + lane] = sl;
+    s_ln[64 + lane] = pm;
+
+    const int ilo = sf - P, klo = sf - P + 1;   // this lane's first control point and knot
+    float4 Qw[PB], tau[PB];
+    float kacc[KW > 0 ? KW : 1];
+#pragma unroll
+    for (int r = 0; r < PB; ++r) { Qw[r] = f4zero(); tau[r] = f4zero(); }
+#pragma unroll
+    for (int k = 0; k < (KW > 0 ? KW : 1); ++k) kacc[k] = 0.f;
+    float lossacc = 0.f, uprev = -3.0e38f;
+    int cur = -1;
+
+    auto retire_row = [&](int i, float4 v) {
+        if (i > pm) s_A[i] = v;
+        else if (i - ilo <= P) s_Aov[lane * PB + (i - ilo)] = v;
+    };
+    auto retire_knot = [&](int kk, float v) {
+        if (kk > pm + P) s_K[kk] = v;
+        else if (kk - klo < KW) s_Kov[lane * KW + (kk - klo)] = v;
+    };
+    // move the window to span s (s >= cur): retire what leaves, load what enters
+    auto advance = [&](int s) {
+        if (cur < 0) {
+#pragma unroll
+            for (int r = 0; r < PB; ++r) Qw[r] = homog(__ldg(gP + s - P + r));
+            cur = s;
+            return;
+        }
+        while (cur < s) {
+            if constexpr (GRAD) {
+                retire_row(cur - P, tau[0]);
+                if constexpr (KNOTS) retire_knot(cur - P + 1, kacc[0]);
+            }
+#pragma unroll
+            for (int r = 0; r < P; ++r) { Qw[r] = Qw[r + 1]; tau[r] = tau[r + 1]; }
+            tau[P] = f4zero();
+            if constexpr (KNOTS) {
+#pragma unroll
+                for (int k = 0; k + 1 < KW; ++k) kacc[k] = kacc[k + 1];
+                kacc[KW - 1] = 0.f;
+            }
+            ++cur;
+            if (cur > s - PB) Qw[P] = homog(__ldg(gP + cur));   // only the last P+1 matter
+        }
+    };
+
+    const bool has_pts = kp.pts != nullptr;
+    // one sample: span, basis, point, MSE and the adjoint accumulations
+    auto process = [&](int b, float u, float gx, float gy, float gz) {
+        if (!(u >= ulo && u <= uhi)) err |= kErrDomain;
+        if (u < uprev) err |= kErrOrder;
+        uprev = u;
+        u = fminf(fmaxf(u, ulo), uhi);
+        int s = cur < 0 ? sf : cur;
+        if (s < n && !(u < s_kn[s + 1])) s = find_span(n, P, u, s_kn);
+        advance(s);
+        float N[PB];
+        basis_funs<P>(s, u, s_kn, N);
+        float4 Cw = f4zero();
+#pragma unroll
+        for (int r = 0; r < PB; ++r) Cw = fma4(N[r], Qw[r], Cw);
+        const float inv = rcp_approx(Cw.w);
+        const float Sx = Cw.x * inv, Sy = Cw.y * inv, Sz = Cw.z * inv;
+        if (has_pts) {
+            float* o = kp.pts + 3 * (it.pts + b);
+            o[0] = Sx; o[1] = Sy; o[2] = Sz;
+        }
+        if constexpr (GRAD) {
+            float ginv = inv;
+            if constexpr (MSE) {
+                gx = Sx - gx; gy = Sy - gy; gz = Sz - gz;
+                lossacc = fmaf(gx, gx, fmaf(gy, gy, fmaf(gz, gz, lossacc)));
+                ginv *= kp.grad_scale;
+            }
+            const float lx = gx * ginv, ly = gy * ginv, lz = gz * ginv;
+            const float4 lam = make_float4(lx, ly, lz, -fmaf(Sx, lx, fmaf(Sy, ly, Sz * lz)));
+#pragma unroll
+            for (int r = 0; r < PB; ++r) tau[r] = fma4(N[r], lam, tau[r]);
+            if constexpr (KNOTS) {
+                float beta[PB];
+#pragma unroll
+                for (int r = 0; r < PB; ++r) beta[r] = dot4(Qw[r], lam);
+                float dk[2 * P + 1];
+                basis_knot_vjp<P>(s, u, s_kn, beta, dk);
+#pragma unroll
+                for (int q = 0; q < KW; ++q) kacc[q] += dk[q];
+            }
+        }
+    };
+
+    // this lane's chunk offsets in a ring stage (floats)
+    const int o0 = 4 * (0 ^ swz), o1 = 4 * (1 ^ swz), o2 = 4 * (2 ^ swz), o3 = 4 * (3 ^ swz);
+    for (int k = 0; k < rounds; ++k) {
+        cp_async_wait<1>();   // round k has landed (round k+1 may be in flight)
+        const float* rb = s_ring + ((k & 1) * 32 + lane) * 16;
+        const int bb = b0 + k * R;
+        // target word w = 3j + c of the round sits in chunk 1 + w / 4
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            if (bb + j < b1) {
+                float g[3] = {0.f, 0.f, 0.f};
+                if constexpr (GRAD) {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        const int w = 3 * j + c;
+                        const int oc = (w < 4) ? o1 : (w < 8) ? o2 : o3;
+                        g[c] = rb[oc + (w & 3)];
+                    }
+                }
+                process(bb + j, rb[o0 + j], g[0], g[1], g[2]);
+            }
+        }
+        __syncwarp();
+        issue(k + 2);   // the stage just read is refilled two rounds ahead
+    }
+    if constexpr (GRAD) {
+        if (cur >= 0) {
+#pragma unroll
+            for (int r = 0; r < PB; ++r) retire_row(cur - P + r, tau[r]);
+            if constexpr (KNOTS) {
+#pragma unroll
+                for (int q = 0; q < KW; ++q) retire_knot(cur - P + 1 + q, kacc[q]);
+            }
+        }
+    }
+    cp_async_wait<0>();
+    if (err) atomicOr(&kp.hdr->error, err);
+    __syncwarp();
+    if constexpr (!GRAD) return;
+
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) lossacc += __shfl_xor_sync(0xffffffffu, lossacc, o);
+    if (lane == 0 && kp.loss_items != nullptr) kp.loss_items[item] = lossacc;
+    __syncwarp();
+
+    // First lane whose last span reaches index x (spans of active lanes are sorted).
+    auto first_lane = [&](int x) {
+        int lo = 0, hi = nact;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (s_ln[32 + mid] < x) lo = mid + 1; else hi = mid;
+        }
+        return lo;
+    };
+
+    if (kp.grad_ctrl != nullptr || kp.fit) {
+        float lr_t, isb2;
+        adam_corrections(kp, it, lr_t, isb2);
+        constexpr int EB = 2;
+        for (int i0 = lane; i0 < nc; i0 += EB * 32) {
+            float4 a[EB], c[EB], mm[EB], vv[EB];
+#pragma unroll
+            for (int e = 0; e < EB; ++e) {
+                const int i = i0 + 32 * e;
+                a[e] = c[e] = mm[e] = vv[e] = f4zero();
+                if (i >= nc) continue;
+                c[e] = gP[i];
+                if (kp.fit) { mm[e] = kp.adam_m[it.ctrl + i]; vv[e] = kp.adam_v[it.ctrl + i]; }
+                bool first = true;
+                for (int l = first_lane(i); l < nact && s_ln[l] - P <= i; ++l) {
+                    if (first) {
+                        a[e] = s_A[i];
+                        first = false;
+                    } else {
+                        const int d = i - (s_ln[l] - P);
+                        if (d >= 0 && d < PB) {
+                            const float4 v = s_Aov[l * PB + d];
+                            a[e].x += v.x; a[e].y += v.y; a[e].z += v.z; a[e].w += v.w;
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int e = 0; e < EB; ++e) {
+                const int i = i0 + 32 * e;
+                if (i < nc) finish_point(kp, it.ctrl + i, c[e], a[e], mm[e], vv[e], lr_t, isb2);
+            }
+        }
+    }
+    if constexpr (KNOTS) {
+        if (kp.grad_knots != nullptr) {
+            for (int kk = lane; kk < nk; kk += 32) {
+                float acc = 0.f;
+                if (kk >= P + 1 && kk <= n) {   // the p+1 end knots on each side get 0
+                    bool first = true;
+                    for (int l = first_lane(kk - P); l < nact && s_ln[l] - P + 1 <= kk; ++l) {
+                        if (first) {
+                            acc = s_K[kk];
+                            first = false;
+                        } else {
+                            const int d = kk - (s_ln[l] - P + 1);
+                            if (d >= 0 && d < KW) acc += s_Kov[l * KW + d];
+                        }
+                    }
+                }
+                kp.grad_knots[it.knot_v + kk] = acc;
+            }
+        }
+    }
+    __syncwarp();
+}
+
+template <int P, bool GRAD, bool KNOTS, bool MSE>
+__global__ void __launch_bounds__(32 * kCurveWarps, 4) curves_kernel(const __grid_constant__ KParams kp)
+{
+    extern __shared__ float4 smem4[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned char* wsm = reinterpret_cast<unsigned char*>(smem4) + warp * kp.c_wbytes;
+    // the first curve of each warp is its own index; later ones come from the queue
+    int t = kp.t0 + (int)blockIdx.x * kCurveWarps + warp;
+    while (t < kp.t1) {
+        curve_body<P, GRAD, KNOTS, MSE>(kp, t, wsm);
+        int nt = 0;
+        if (lane == 0) nt = kp.t0 + (int)gridDim.x * kCurveWarps + (int)atomicAdd(kp.queue, 1u);
+        t = __shfl_sync(0xffffffffu, nt, 0);
+    }
+    __syncthreads();
+    // the last CTA out rearms the queue for the next launch on this workspace
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned e = atomicAdd(kp.queue + 1, 1u);
+        if (e + 1 == gridDim.x) {
+            kp.queue[0] = 0u;
+            kp.queue[1] = 0u;
+            __threadfence();
+        }
+    }
+}
+
+}  // namespace nurbs

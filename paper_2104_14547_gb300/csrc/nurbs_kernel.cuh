@@ -8,14 +8,15 @@ namespace nurbs {
 template <int P, int Q, bool GRAD, bool KNOTS, bool MSE>
 __global__ void __launch_bounds__(256, 2) tiles_kernel(const __grid_constant__ KParams kp)
 {
+    // the first tile of each CTA is its own index; later ones come from the queue
     __shared__ int s_t;
-    for (;;) {
-        if (threadIdx.x == 0) s_t = kp.t0 + (int)atomicAdd(kp.queue, 1u);
-        __syncthreads();
-        const int t = s_t;
-        __syncthreads();
-        if (t >= kp.t1) break;
+    int t = kp.t0 + (int)blockIdx.x;
+    while (t < kp.t1) {
         tile_body<P, Q, GRAD, KNOTS, MSE>(kp, t);
+        if (threadIdx.x == 0) s_t = kp.t0 + (int)gridDim.x + (int)atomicAdd(kp.queue, 1u);
+        __syncthreads();
+        t = s_t;
+        __syncthreads();
     }
     // the last CTA out rearms the queue for the next launch on this workspace
     if (threadIdx.x == 0) {
@@ -72,5 +73,7 @@ KernelVariant variant_p2(int v, int q);
 KernelVariant variant_p3(int v, int q);
 KernelVariant variant_p4(int v, int q);
 KernelVariant variant_p5(int v, int q);
+// Curve kernels (one warp per curve) of degree p, defined in k_curve.cu.
+KernelVariant curve_variant(int v, int p);
 
 }  // namespace nurbs

@@ -1,7 +1,7 @@
 // Device-side tables of a bound plan (shared by the host planner and the
 // kernels).  Everything lives in the caller's workspace:
 //
-//   [0, 256)           WsHeader: error word, one persistent-queue pair per degree group
+//   [0, 512)           WsHeader: error word, one persistent-queue pair per kernel group
 //   items_off          ItemDev[count]
 //   tiles_off          TileDev[ntiles]
 //   counts_off         uint32 per item: tiles finished in the current launch
@@ -20,16 +20,17 @@
 
 namespace nurbs {
 
-constexpr int kHeaderBytes = 256;
+constexpr int kHeaderBytes = 512;
 
-constexpr int kMaxGroups = 30;   // distinct (p, q) pairs: p in 0..5, q in 1..5
+constexpr int kMaxGroups = 30;   // distinct (p, q) pairs of the tile kernels: p in 0..5, q in 1..5
+constexpr int kCurveGroups = 5;  // curve-kernel groups: degree 1..5
 
 struct WsHeader {
     unsigned int error;                  // bit k set <=> nurbs_status k raised on the device
     unsigned int pad0;
-    unsigned int queue[2 * kMaxGroups];  // per degree group: next tile, CTAs finished
-    unsigned int pad1[2];
+    unsigned int queue[2 * (kMaxGroups + kCurveGroups)];   // per group: next tile, CTAs finished
 };
+static_assert(sizeof(WsHeader) <= kHeaderBytes, "workspace header");
 
 struct ItemDev {
     int p, q, n1, m1, nu, nv;
@@ -42,7 +43,7 @@ struct ItemDev {
     int curve;       // 1: a curve item mapped onto the v direction (p == 0, n1 == 1)
     int adam_step;   // fit step: this item's Adam step (0 = the launch's)
     int smemA;       // single-tile item whose homogeneous adjoint stays in shared memory
-    int pad2;
+    int ck;          // curve run by the curve kernels (one warp per curve, one tile)
     long long knot_u, knot_v, ctrl, param_u, param_v, pts;
 };
 

@@ -70,9 +70,10 @@ struct KParams {
     // shared-memory carve-up in bytes (host-computed for the plan's largest tile)
     int R, C;
     int off_misc, off_su, off_u, off_nu, off_sv, off_v, off_nv, off_stage, off_beta, off_duc, off_dvc, off_ring,
-        off_jb, off_win, off_run, off_crun, off_knots, off_w, off_acc, off_sa;
+        off_jb, off_win, off_run, off_knots, off_w, off_acc, off_sa;
 
     int acc_cap;             // bytes available to the final reduction from off_acc
+    int c_mc, c_wbytes;      // curve kernels: control-point capacity, shared bytes per warp
 };
 
 __device__ __forceinline__ float4 f4zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
@@ -200,18 +201,16 @@ __device__ __forceinline__ void adam_corrections(const KParams& kp, const ItemDe
     }
 }
 
-// Control point e of an item from its homogeneous adjoint a: Cartesian gradient
-// and, in a fit step, the Adam update of the point, its weight and the moments.
-__device__ __forceinline__ void finish_ctrl(const KParams& kp, const ItemDev& it, int e, float4 a, float lr_t,
-                                            float isb2)
+// Control point idx (Cartesian c) from its homogeneous adjoint a: Cartesian
+// gradient and, in a fit step, the Adam update of the point, its weight and the
+// moments mm, vv (loaded by the caller).
+__device__ __forceinline__ void finish_point(const KParams& kp, long long idx, float4 c, float4 a, float4 mm,
+                                             float4 vv, float lr_t, float isb2)
 {
-    const long long idx = it.ctrl + e;
-    const float4 c = kp.ctrl[idx];
     // Pw = (w x, w y, w z, w): dL/dx = w A.x, ..., dL/dw = x A.x + y A.y + z A.z + A.w
     const float4 g = make_float4(c.w * a.x, c.w * a.y, c.w * a.z, fmaf(c.x, a.x, fmaf(c.y, a.y, fmaf(c.z, a.z, a.w))));
     if (kp.grad_ctrl != nullptr) kp.grad_ctrl[idx] = g;
     if (kp.fit) {
-        float4 mm = kp.adam_m[idx], vv = kp.adam_v[idx];
         const float ob1 = 1.f - kp.b1, ob2 = 1.f - kp.b2;
         mm.x = fmaf(kp.b1, mm.x, ob1 * g.x); vv.x = fmaf(kp.b2, vv.x, ob2 * g.x * g.x);
         mm.y = fmaf(kp.b1, mm.y, ob1 * g.y); vv.y = fmaf(kp.b2, vv.y, ob2 * g.y * g.y);
@@ -228,43 +227,68 @@ __device__ __forceinline__ void finish_ctrl(const KParams& kp, const ItemDev& it
     }
 }
 
+__device__ __forceinline__ void finish_ctrl(const KParams& kp, const ItemDev& it, int e, float4 a, float lr_t,
+                                            float isb2)
+{
+    const long long idx = it.ctrl + e;
+    const float4 c = kp.ctrl[idx];
+    float4 mm = f4zero(), vv = f4zero();
+    if (kp.fit) { mm = kp.adam_m[idx]; vv = kp.adam_v[idx]; }
+    finish_point(kp, idx, c, a, mm, vv, lr_t, isb2);
+}
+
 // The only tile of its item, with A kept in shared memory: the net block holds,
 // for each control row, the first covering unit's block, and the overflow block
 // of unit u (pb rows from its first row) its share of rows an earlier unit also
 // covers.  s_units[3u..3u+2] = first control row, row count and the last control
 // row of the earlier units; columns [jlo, jlo+cw) were written.  Units are added
-// in order and every control point is finished.
-static __device__ __noinline__ void final_ctrl_smem(const KParams& kp, int item, int nwr, int pb,
-                                                    const int* s_units, int jlo, int cw)
+// in order and every control point is finished; s_net, when not null, is the
+// item's control net staged in shared memory.  Each thread handles four points
+// per pass with all their loads issued first.
+__device__ __forceinline__ void final_ctrl_smem(const KParams& kp, const ItemDev& it, int nwr, int pb,
+                                                const int* s_units, int jlo, int cw, const float4* s_net)
 {
     extern __shared__ float4 smem4[];
     unsigned char* smem = reinterpret_cast<unsigned char*>(smem4);
-    const ItemDev it = kp.items[item];
     if (kp.grad_ctrl == nullptr && !kp.fit) return;
-    const int m1 = it.m1, ncp = it.n1 * m1;
+    const int m1 = it.m1, ncp = it.n1 * m1, bs = blockDim.x;
     const float4* sB = reinterpret_cast<const float4*>(smem + kp.off_sa);
     const float4* sO = sB + ncp;
     float lr_t, isb2;
     adam_corrections(kp, it, lr_t, isb2);
-    for (int e = threadIdx.x; e < ncp; e += blockDim.x) {
-        const int i = e / m1, j = e - i * m1;
-        float4 a = f4zero();
-        if (j >= jlo && j < jlo + cw) {
-            bool cov = false;
-            for (int u = 0; u < nwr; ++u) {
-                const int ilo = s_units[3 * u], nr = s_units[3 * u + 1];
-                cov |= nr > 0 && i >= ilo && i < ilo + nr;
-            }
-            if (cov) a = sB[e];
-            for (int u = 1; u < nwr; ++u) {
-                const int ilo = s_units[3 * u], nr = s_units[3 * u + 1], pm = s_units[3 * u + 2];
-                if (nr > 0 && i >= ilo && i < ilo + nr && i <= pm) {
-                    const float4 v = sO[(u * pb + i - ilo) * m1 + j];
-                    a.x += v.x; a.y += v.y; a.z += v.z; a.w += v.w;
+    constexpr int EB = 4;
+    for (int e0 = threadIdx.x; e0 < ncp; e0 += EB * bs) {
+        float4 a[EB], c[EB], mm[EB], vv[EB];
+#pragma unroll
+        for (int k = 0; k < EB; ++k) {
+            const int e = e0 + k * bs;
+            a[k] = c[k] = mm[k] = vv[k] = f4zero();
+            if (e >= ncp) continue;
+            const long long idx = it.ctrl + e;
+            c[k] = s_net != nullptr ? s_net[e] : kp.ctrl[idx];
+            if (kp.fit) { mm[k] = kp.adam_m[idx]; vv[k] = kp.adam_v[idx]; }
+            const int i = e / m1, j = e - i * m1;
+            if (j >= jlo && j < jlo + cw) {
+                bool cov = false;
+                for (int u = 0; u < nwr; ++u) {
+                    const int ilo = s_units[3 * u], nr = s_units[3 * u + 1];
+                    cov |= nr > 0 && i >= ilo && i < ilo + nr;
+                }
+                if (cov) a[k] = sB[e];
+                for (int u = 1; u < nwr; ++u) {
+                    const int ilo = s_units[3 * u], nr = s_units[3 * u + 1], pm = s_units[3 * u + 2];
+                    if (nr > 0 && i >= ilo && i < ilo + nr && i <= pm) {
+                        const float4 v = sO[(u * pb + i - ilo) * m1 + j];
+                        a[k].x += v.x; a[k].y += v.y; a[k].z += v.z; a[k].w += v.w;
+                    }
                 }
             }
         }
-        finish_ctrl(kp, it, e, a, lr_t, isb2);
+#pragma unroll
+        for (int k = 0; k < EB; ++k) {
+            const int e = e0 + k * bs;
+            if (e < ncp) finish_point(kp, it.ctrl + e, c[k], a[k], mm[k], vv[k], lr_t, isb2);
+        }
     }
 }
 
@@ -470,7 +494,8 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
             for (int r = tid; r < nrows; r += bs) cp_async4(s_u + r, kp.params + it.param_u + tl.row0 + r);
         for (int c = tid; c < ncols; c += bs) cp_async4(s_v + c, kp.params + it.param_v + tl.col0 + c);
     }
-    // the whole control net rides along when it fits (else the tile's window follows later)
+    // the whole control net rides along when it fits (else the tile's window follows
+    // later); it stays Cartesian (x, y, z, w), which the final pass also reads
     float4* s_win = reinterpret_cast<float4*>(smem + kp.off_win);
     const int ncp = it.n1 * it.m1;
     const bool net_staged = !empty && ncp <= kWinCap;
@@ -482,10 +507,14 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
     cp_async_commit();
     cp_async_wait<0>();
     __syncthreads();
-    if (net_staged)
-        for (int e = tid; e < ncp; e += bs) s_win[e] = homog(s_win[e]);
 
-    // ---- device checks: knot vectors once per item, samples in the domain and in order
+    // ---- one pass over rows and columns: device checks (knot vectors once per item,
+    // samples in the domain and in order) and each sample row's and column's span and
+    // basis (Sec. 3.1 steps 1-2); samples outside the domain are clamped to it (and
+    // reported), and the clamped values are recomputed where needed
+    const float ulo = (P > 0) ? s_knU[P] : 0.f, uhi = (P > 0) ? s_knU[n + 1] : 0.f;
+    const float vlo = s_knV[Q], vhi = s_knV[m + 1];
+    const int npro_r = empty ? 0 : nrows, npro_c = empty ? 0 : ncols;   // empty tiles skip the tables
     if (!empty) {
         unsigned e = 0;
         if (tl.tidx == 0) {
@@ -498,74 +527,73 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
                 if (s_knV[k] > s_knV[k + 1]) e |= kErrKnots;
             if (tid == 0 && !(s_knV[m] < s_knV[m + 1])) e |= kErrKnots;
         }
-        if constexpr (P > 0) {
-            const float lo = s_knU[P], hi = s_knU[n + 1];
-            for (int r = tid; r < nrows; r += bs) {
-                const float u0 = s_u[r];
-                if (!(u0 >= lo && u0 <= hi)) e |= kErrDomain;
-                if (r > 0 && s_u[r - 1] > u0) e |= kErrOrder;
-            }
-        }
-        {
-            const float lo = s_knV[Q], hi = s_knV[m + 1];
-            for (int c = tid; c < ncols; c += bs) {
+        for (int x = tid; x < npro_r + npro_c; x += bs) {
+            if (x < npro_r) {
+                const int r = x;
+                float N[PB];
+                int s = 0;
+                float uc = 0.f;
+                if constexpr (P > 0) {
+                    const float u0 = s_u[r];
+                    if (!(u0 >= ulo && u0 <= uhi)) e |= kErrDomain;
+                    if (r > 0 && s_u[r - 1] > u0) e |= kErrOrder;
+                    uc = fminf(fmaxf(u0, ulo), uhi);
+                    s = find_span(n, P, uc, s_knU);
+                }
+                basis_funs<P>(s, uc, s_knU, N);
+                s_su[r] = s;
+#pragma unroll
+                for (int k = 0; k < PB; ++k) s_nu[r * SU + k] = N[k];
+            } else {
+                const int c = x - npro_r;
                 const float v0 = s_v[c];
-                if (!(v0 >= lo && v0 <= hi)) e |= kErrDomain;
+                if (!(v0 >= vlo && v0 <= vhi)) e |= kErrDomain;
                 if (c > 0 && s_v[c - 1] > v0) e |= kErrOrder;
+                const float vc = fminf(fmaxf(v0, vlo), vhi);
+                float N[QB];
+                const int s = find_span(m, Q, vc, s_knV);
+                basis_funs<Q>(s, vc, s_knV, N);
+                s_sv[c] = s;
+#pragma unroll
+                for (int k = 0; k < QB; ++k) s_nv[c * SV + k] = N[k];
             }
         }
         if (e) atomicOr(&kp.hdr->error, e);
     }
     __syncthreads();
 
-    // ---- row prologue: span and u-basis per sample row (Sec. 3.1 steps 1-2);
-    // samples outside the domain are clamped to it (and reported above)
-    const int npro_r = empty ? 0 : nrows, npro_c = empty ? 0 : ncols;   // empty tiles skip the tables
-    for (int r = tid; r < npro_r; r += bs) {
-        float N[PB];
-        int s = 0;
-        float u0 = 0.f;
-        if constexpr (P > 0) {
-            u0 = fminf(fmaxf(s_u[r], s_knU[P]), s_knU[n + 1]);
-            s = find_span(n, P, u0, s_knU);
-        }
-        basis_funs<P>(s, u0, s_knU, N);
-        s_su[r] = s;
-        s_u[r] = u0;
-#pragma unroll
-        for (int k = 0; k < PB; ++k) s_nu[r * SU + k] = N[k];
-    }
-    // ---- column prologue: span and v-basis per sample column
-    for (int c = tid; c < npro_c; c += bs) {
-        float N[QB];
-        const float v0 = fminf(fmaxf(s_v[c], s_knV[Q]), s_knV[m + 1]);
-        const int s = find_span(m, Q, v0, s_knV);
-        basis_funs<Q>(s, v0, s_knV, N);
-        s_sv[c] = s;
-        s_v[c] = v0;
-#pragma unroll
-        for (int k = 0; k < QB; ++k) s_nv[c * SV + k] = N[k];
-    }
-    __syncthreads();
     // ---- the sliding windows need non-decreasing spans; anything else is refused.
-    // Rows with equal u-span form runs; s_run[r] is the end of the run holding r.
+    // Same pass: rows with equal u-span form runs (s_run[r] = end of the run holding
+    // r), and for control column jlo_t + jj of the A contraction the sample columns
+    // [lo, lo+len) feeding it.  The contraction A[i][j] = sum_b Nv_{j-s_v(b)+Q}(b)
+    // tau[i](b) is a fixed sparse matrix: its weights for column jj sit at
+    // s_w[s_joff[jj] ...] (every sample feeds Q+1 columns, so ncols*(Q+1) weights).
     int* s_run = reinterpret_cast<int*>(smem + kp.off_run);
-    int* s_crun = reinterpret_cast<int*>(smem + kp.off_crun);
+    int2* s_jb = reinterpret_cast<int2*>(smem + kp.off_jb);
+    int* s_joff = reinterpret_cast<int*>(smem + kp.off_w);
+    float* s_w = reinterpret_cast<float*>(smem + kp.off_w) + kJbCap;
+    const int jlo_0 = empty ? 0 : s_sv[0] - Q;
+    const int cw_0 = empty ? 0 : max(0, s_sv[ncols - 1] - jlo_0 + 1);
+    const int njb = GRAD ? min(cw_0, kJbCap) : 0;
     {
-        bool bad = false;
-        for (int r = tid; r < npro_r; r += bs) {
-            if (r > 0) bad |= s_su[r] < s_su[r - 1];
-            int re = r + 1;
-            while (re < nrows && s_su[re] == s_su[r]) ++re;
-            s_run[r] = re;
+        bool badl = false;
+        for (int x = tid; x < npro_r + npro_c + njb; x += bs) {
+            if (x < npro_r) {
+                const int r = x;
+                if (r > 0) badl |= s_su[r] < s_su[r - 1];
+                int re = r + 1;
+                while (re < nrows && s_su[re] == s_su[r]) ++re;
+                s_run[r] = re;
+            } else if (x < npro_r + npro_c) {
+                const int c = x - npro_r;
+                if (c > 0) badl |= s_sv[c] < s_sv[c - 1];
+            } else {
+                const int jj = x - npro_r - npro_c;
+                const int lo = lower_bound_i(s_sv, ncols, jlo_0 + jj);
+                s_jb[jj] = make_int2(lo, lower_bound_i(s_sv, ncols, jlo_0 + jj + Q + 1) - lo);
+            }
         }
-        for (int c = tid; c < npro_c; c += bs) {
-            if (c > 0) bad |= s_sv[c] < s_sv[c - 1];
-            int ce = c + 1;
-            while (ce < ncols && s_sv[ce] == s_sv[c]) ++ce;
-            s_crun[c] = ce;
-        }
-        if (bad) { s_flag[0] = 1; atomicOr(&kp.hdr->error, kErrOrder); }
+        if (badl) { s_flag[0] = 1; atomicOr(&kp.hdr->error, kErrOrder); }
     }
     __syncthreads();
     const bool bad = s_flag[0] != 0;
@@ -581,40 +609,29 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
 #pragma unroll
     for (int h = 0; h < QB; ++h) Gam[h] = 0.f;
 
-    // per-tile table of the sample-column range [lo, hi) feeding each control column
-    // jlo_t + jj of the A contraction (all units of a tile span the same columns)
-    const int jlo_t = bad ? 0 : s_sv[0] - Q;
-    const int cw_t = bad ? 0 : s_sv[ncols - 1] - jlo_t + 1;
-    // The contraction A[i][j] = sum_b Nv_{j-s_v(b)+Q}(b) tau[i](b) as a fixed sparse
-    // matrix: for control column jlo_t + jj, the samples [lo, lo+len) and their weights
-    // at s_w[s_joff[jj] ...] (every sample feeds Q+1 columns, so ncols*(Q+1) weights).
-    int2* s_jb = reinterpret_cast<int2*>(smem + kp.off_jb);
-    int* s_joff = reinterpret_cast<int*>(smem + kp.off_w);
-    float* s_w = reinterpret_cast<float*>(smem + kp.off_w) + kJbCap;
-    const int njb = min(cw_t, kJbCap);
+    // column range of the A contraction (all units of a tile span the same columns)
+    const int jlo_t = bad ? 0 : jlo_0;
+    const int cw_t = bad ? 0 : cw_0;
     if constexpr (GRAD) {
-        for (int jj = tid; jj < njb; jj += bs) {
-            const int lo = lower_bound_i(s_sv, ncols, jlo_t + jj);
-            s_jb[jj] = make_int2(lo, lower_bound_i(s_sv, ncols, jlo_t + jj + Q + 1) - lo);
-        }
-        __syncthreads();
-        if (tid == 0) {
-            int o = 0;
-            for (int jj = 0; jj < njb; ++jj) { s_joff[jj] = o; o += s_jb[jj].y; }
-        }
-        __syncthreads();
-        for (int jj = tid; jj < njb; jj += bs) {
-            const int2 r2 = s_jb[jj];
-            const int j = jlo_t + jj;
-            float* w = s_w + s_joff[jj];
-            for (int q = 0; q < r2.y; ++q) {
-                const int b = r2.x + q;
-                w[q] = s_nv[b * SV + (j - s_sv[b] + Q)];
+        // exclusive prefix of the columns' sample counts (one warp, shuffle scan)
+        if (warp == 0 && !bad) {
+            int carry = 0;
+            for (int base = 0; base < njb; base += 32) {
+                const int jj = base + lane;
+                const int len = jj < njb ? s_jb[jj].y : 0;
+                int incl = len;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                if (jj < njb) s_joff[jj] = carry + incl - len;
+                carry += __shfl_sync(0xffffffffu, incl, 31);
             }
         }
     }
     // otherwise the tile's window of control points, rows [iwl, iwl+rw) x columns
-    // [jlo_t, jlo_t+cw_t), when it fits; both are held as homogeneous points
+    // [jlo_t, jlo_t+cw_t), when it fits
     const int iwl = (bad || net_staged) ? 0 : s_su[0] - P;
     const int rw_t = bad ? 0 : s_su[nrows - 1] - (s_su[0] - P) + 1;
     const bool win_only = !bad && !net_staged && rw_t * cw_t <= kWinCap;
@@ -628,15 +645,24 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
             cp_async16(reinterpret_cast<float*>(s_win + e), reinterpret_cast<const float*>(src + (long long)ii * it.m1 + jj));
         }
         cp_async_commit();
-        cp_async_wait<0>();
-        __syncthreads();
-        for (int e = tid; e < rw_t * cw_t; e += bs) s_win[e] = homog(s_win[e]);
     }
+    __syncthreads();
+    if constexpr (GRAD) {
+        // sample b's basis value h is the weight of column s_v(b) - Q + h
+        if (!bad) {
+            for (int x = tid; x < ncols * QB; x += bs) {
+                const int b = x / QB, h = x - b * QB;
+                const int jj = s_sv[b] - Q + h - jlo_t;
+                if (jj < njb) s_w[s_joff[jj] + (b - s_jb[jj].x)] = s_nv[b * SV + h];
+            }
+        }
+    }
+    if (win_only) cp_async_wait<0>();
     __syncthreads();
 
     if (uactive) {
         const int svb = s_sv[blc];
-        const float vb = s_v[blc];
+        const float vb = fminf(fmaxf(s_v[blc], vlo), vhi);
         float Nv[QB];
 #pragma unroll
         for (int h = 0; h < QB; ++h) Nv[h] = s_nv[blc * SV + h];
@@ -645,22 +671,23 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
 
         const float4* wbase = s_win + (svb - Q - w_j0) - iwl * w_stride;   // window element (i, column of h = 0)
         auto computeQ = [&](int i) -> float4 {
+            // Qw = sum_h Nv_h (w x, w y, w z, w) of row i's Q+1 control points
             float4 acc = f4zero();
+            auto add = [&](float nv, float4 c) {
+                const float wn = nv * c.w;
+                acc.x = fmaf(wn, c.x, acc.x);
+                acc.y = fmaf(wn, c.y, acc.y);
+                acc.z = fmaf(wn, c.z, acc.z);
+                acc.w += wn;
+            };
             if (win) {
                 const float4* wr_ = wbase + i * w_stride;
 #pragma unroll
-                for (int h = 0; h < QB; ++h) acc = fma4(Nv[h], wr_[h], acc);
+                for (int h = 0; h < QB; ++h) add(Nv[h], wr_[h]);
             } else {
                 const float4* cr = cbase + i * m1;
 #pragma unroll
-                for (int h = 0; h < QB; ++h) {
-                    const float4 c = __ldg(cr + h);
-                    const float wn = Nv[h] * c.w;
-                    acc.x = fmaf(wn, c.x, acc.x);
-                    acc.y = fmaf(wn, c.y, acc.y);
-                    acc.z = fmaf(wn, c.z, acc.z);
-                    acc.w += wn;
-                }
+                for (int h = 0; h < QB; ++h) add(Nv[h], __ldg(cr + h));
             }
             return acc;
         };
@@ -720,7 +747,7 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
                 if (win) {
                     const float4* wr_ = wbase + i * w_stride;
 #pragma unroll
-                    for (int h = 0; h < QB; ++h) Gam[h] += dot4(tv, wr_[h]);
+                    for (int h = 0; h < QB; ++h) Gam[h] += dot4(tv, homog(wr_[h]));
                 } else {
                     const float4* cr = cbase + i * m1;
 #pragma unroll
@@ -763,6 +790,7 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
 
         const int rstride = 3 * it.nv;                        // floats between sample rows
         const bool store = cvalid && kp.pts != nullptr;
+        const bool full = nvw == 32;   // every lane of the warp holds a valid column
         float* orow = kp.pts != nullptr ? kp.pts + 3 * (prow0 + lane) : nullptr;   // row 0 of this lane
         float* s_beta_w = reinterpret_cast<float*>(smem + kp.off_beta) + (wc * kp.R) * SU;
 
@@ -800,18 +828,22 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
                 for (int q = 0; q < NR; ++q) {
                     const float* gp = ring + ((r + q - ra) & (kRing - 1)) * 96 + 3 * lane;
                     float gx, gy, gz;
+                    float ginv = inv[q];   // dL/dS = ginv * W * (gx, gy, gz)
                     if constexpr (MSE) {
                         float dx = Sx[q] - gp[0], dy = Sy[q] - gp[1], dz = Sz[q] - gp[2];
-                        dx = cvalid ? dx : 0.f; dy = cvalid ? dy : 0.f; dz = cvalid ? dz : 0.f;
+                        if (!full) { dx = cvalid ? dx : 0.f; dy = cvalid ? dy : 0.f; dz = cvalid ? dz : 0.f; }
                         lossacc = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, lossacc)));
-                        gx = kp.grad_scale * dx; gy = kp.grad_scale * dy; gz = kp.grad_scale * dz;
+                        gx = dx; gy = dy; gz = dz;
+                        ginv *= kp.grad_scale;
+                    } else if (full) {
+                        gx = gp[0]; gy = gp[1]; gz = gp[2];
                     } else {
                         gx = cvalid ? gp[0] : 0.f; gy = cvalid ? gp[1] : 0.f; gz = cvalid ? gp[2] : 0.f;
                     }
                     float* o = orow + (r + q) * rstride;
                     if (store) { o[0] = Sx[q]; o[1] = Sy[q]; o[2] = Sz[q]; }
                     // lambda = dL/dS' for S' = (NR, W): (g / W, -S.g / W)
-                    const float gbx = gx * inv[q], gby = gy * inv[q], gbz = gz * inv[q];
+                    const float gbx = gx * ginv, gby = gy * ginv, gbz = gz * ginv;
                     lam[q] = make_float4(gbx, gby, gbz, -fmaf(Sx[q], gbx, fmaf(Sy[q], gby, Sz[q] * gbz)));
                 }
                 __syncwarp();   // these slots are refilled by later requests
@@ -862,12 +894,12 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
                 }
             }
             if constexpr (KNOTS) {
+                // the column's Gamma of this unit; the knot derivative is linear in it, so
+                // the epilogue sums the units first and differentiates once per column
                 if (cvalid) {
-                    float dk[2 * Q + 1];
-                    basis_knot_vjp<Q>(svb, vb, s_knV, Gam, dk);
-                    float* dv = reinterpret_cast<float*>(smem + kp.off_dvc) + (wr * kp.C + bl) * KV;
+                    float* gv = reinterpret_cast<float*>(smem + kp.off_dvc) + (wr * kp.C + bl) * KV;
 #pragma unroll
-                    for (int k = 0; k < 2 * Q; ++k) dv[k] = dk[k];
+                    for (int h = 0; h < QB; ++h) gv[h] = Gam[h];
                 }
             }
         }
@@ -907,94 +939,92 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
         if constexpr (KNOTS) {
             if (!bad) {
                 const int nwc_valid = (ncols + 31) / 32;
+                const int ngv = min(nwr, (nrows + rpg - 1) / rpg);   // row groups that hold rows
                 float* s_duc = reinterpret_cast<float*>(smem + kp.off_duc);
                 float* s_dvc = reinterpret_cast<float*>(smem + kp.off_dvc);
-                // dL/dU: per row, beta summed over the column warps in order, then the
-                // reverse-mode knot derivative of the row's basis
-                if constexpr (P > 0) {
-                    const float* s_beta = reinterpret_cast<const float*>(smem + kp.off_beta);
-                    for (int r = tid; r < nrows; r += bs) {
-                        float bsum[PB];
+                const float* s_beta = reinterpret_cast<const float*>(smem + kp.off_beta);
+                // Reverse-mode knot derivative of each row's u-basis (beta summed over the
+                // column warps in order) and of each column's v-basis (Gamma summed over
+                // the row groups in order), in one pass
+                for (int x = tid; x < nrows + ncols; x += bs) {
+                    if (x < nrows) {
+                        if constexpr (P > 0) {
+                            const int r = x;
+                            float bsum[PB];
 #pragma unroll
-                        for (int k = 0; k < PB; ++k) bsum[k] = 0.f;
-                        for (int w = 0; w < nwc_valid; ++w) {
-                            float bw[PB];
-                            load_basis<PB>(s_beta + (w * kp.R + r) * SU, bw);
+                            for (int k = 0; k < PB; ++k) bsum[k] = 0.f;
+                            for (int w = 0; w < nwc_valid; ++w) {
+                                float bw[PB];
+                                load_basis<PB>(s_beta + (w * kp.R + r) * SU, bw);
 #pragma unroll
-                            for (int k = 0; k < PB; ++k) bsum[k] += bw[k];
-                        }
-                        float dk[2 * P + 1];
-                        basis_knot_vjp<P>(s_su[r], s_u[r], s_knU, bsum, dk);
+                                for (int k = 0; k < PB; ++k) bsum[k] += bw[k];
+                            }
+                            float dk[2 * P + 1];
+                            basis_knot_vjp<P>(s_su[r], fminf(fmaxf(s_u[r], ulo), uhi), s_knU, bsum, dk);
 #pragma unroll
-                        for (int k = 0; k < 2 * P; ++k) s_duc[r * KU + k] = dk[k];
-                    }
-                }
-                __syncthreads();
-                // runs of rows (columns) share a knot window: sum each run first, in order
-                if constexpr (P > 0) {
-                    for (int e = tid; e < nrows * 2 * P; e += bs) {
-                        const int r = e / (2 * P), k = e - r * (2 * P);
-                        if (r > 0 && s_su[r - 1] == s_su[r]) continue;   // not a run start
-                        float acc = 0.f;
-                        for (int q = r; q < s_run[r]; ++q) acc += s_duc[q * KU + k];
-                        s_duc[r * KU + k] = acc;
-                    }
-                }
-                for (int e = tid; e < ncols * 2 * Q; e += bs) {
-                    const int c = e / (2 * Q), k = e - c * (2 * Q);
-                    if (c > 0 && s_sv[c - 1] == s_sv[c]) continue;
-                    float acc = 0.f;
-                    for (int g = 0; g < nwr; ++g) {
-                        if (g * rpg >= nrows) break;
-                        for (int q = c; q < s_crun[c]; ++q) acc += s_dvc[(g * kp.C + q) * KV + k];
-                    }
-                    s_dvc[c * KV + k] = acc;   // row group 0's slot holds the run sum
-                }
-                __syncthreads();
-                if constexpr (P > 0) {
-                    const int ku_lo = s_su[0] - P + 1;
-                    const int nku = s_su[nrows - 1] + P - ku_lo + 1;
-                    if (single) {
-                        for (int kk = tid; kk < it.n1 + P + 1; kk += bs) {
-                            float acc = 0.f;
-                            if (kk >= P + 1 && kk <= it.n1 - 1 && kk >= ku_lo && kk < ku_lo + nku)
-                                for (int r = lower_bound_i(s_su, nrows, kk - P); r < nrows && s_su[r] <= kk + P - 1; r = s_run[r])
-                                    acc += s_duc[r * KU + (kk - (s_su[r] - P + 1))];
-                            kp.grad_knots[it.knot_u + kk] = acc;
+                            for (int k = 0; k < 2 * P; ++k) s_duc[r * KU + k] = dk[k];
                         }
                     } else {
-                        for (int K = tid; K < nku; K += bs) {
-                            const int kk = ku_lo + K;
-                            float acc = 0.f;
-                            for (int r = lower_bound_i(s_su, nrows, kk - P); r < nrows && s_su[r] <= kk + P - 1; r = s_run[r])
-                                acc += s_duc[r * KU + (kk - (s_su[r] - P + 1))];
-                            slot[12 + K] = acc;
+                        const int c = x - nrows;
+                        float G[QB];
+#pragma unroll
+                        for (int h = 0; h < QB; ++h) G[h] = 0.f;
+                        for (int g = 0; g < ngv; ++g) {
+#pragma unroll
+                            for (int h = 0; h < QB; ++h) G[h] += s_dvc[(g * kp.C + c) * KV + h];
                         }
+                        float dk[2 * Q + 1];
+                        basis_knot_vjp<Q>(s_sv[c], fminf(fmaxf(s_v[c], vlo), vhi), s_knV, G, dk);
+#pragma unroll
+                        for (int k = 0; k < 2 * Q; ++k) s_dvc[c * KV + k] = dk[k];   // group 0's slot
                     }
-                    if (tid == 0) { sh[0] = ku_lo; sh[1] = nku; }
-                } else {
-                    if (tid == 0) { sh[0] = 0; sh[1] = 0; }
                 }
+                __syncthreads();
+                // Each knot's derivative: the rows (columns) whose span window holds knot k
+                // form a contiguous range; eight lanes sum it, lane-strided, then in a
+                // fixed tree.  A single-tile item writes every knot of the item (0 at the
+                // p+1 end knots and outside the tile's windows); other tiles write their
+                // windows to the slot.
+                const int ku_lo = (P > 0) ? s_su[0] - P + 1 : 0;
+                const int nku = (P > 0) ? s_su[nrows - 1] + P - ku_lo + 1 : 0;
                 const int kv_lo = s_sv[0] - Q + 1;
                 const int nkv = s_sv[ncols - 1] + Q - kv_lo + 1;
-                if (single) {
-                    for (int kk = tid; kk < it.m1 + Q + 1; kk += bs) {
-                        float acc = 0.f;
-                        if (kk >= Q + 1 && kk <= it.m1 - 1 && kk >= kv_lo && kk < kv_lo + nkv)
-                            for (int c = lower_bound_i(s_sv, ncols, kk - Q); c < ncols && s_sv[c] <= kk + Q - 1; c = s_crun[c])
-                                acc += s_dvc[c * KV + (kk - (s_sv[c] - Q + 1))];
-                        kp.grad_knots[it.knot_v + kk] = acc;
+                const int nkU = single ? nU : nku, nkV = single ? nV : nkv;
+                const int sub = lane >> 3, sl = lane & 7;
+                for (int base = warp * 4; base < nkU + nkV; base += (bs >> 5) * 4) {
+                    const int kx = base + sub;
+                    float acc = 0.f;
+                    bool zero = true;
+                    int kk = 0;
+                    if (kx < nkU) {
+                        kk = single ? kx : ku_lo + kx;
+                        if (kk >= ku_lo && kk < ku_lo + nku && (!single || (kk >= P + 1 && kk <= it.n1 - 1))) {
+                            zero = false;
+                            const int r0 = lower_bound_i(s_su, nrows, kk - P), r1 = lower_bound_i(s_su, nrows, kk + P);
+                            for (int r = r0 + sl; r < r1; r += 8) acc += s_duc[r * KU + (kk - (s_su[r] - P + 1))];
+                        }
+                    } else if (kx < nkU + nkV) {
+                        kk = single ? kx - nkU : kv_lo + (kx - nkU);
+                        if (kk >= kv_lo && kk < kv_lo + nkv && (!single || (kk >= Q + 1 && kk <= it.m1 - 1))) {
+                            zero = false;
+                            const int c0 = lower_bound_i(s_sv, ncols, kk - Q), c1 = lower_bound_i(s_sv, ncols, kk + Q);
+                            for (int c = c0 + sl; c < c1; c += 8) acc += s_dvc[c * KV + (kk - (s_sv[c] - Q + 1))];
+                        }
                     }
-                } else {
-                    for (int K = tid; K < nkv; K += bs) {
-                        const int kk = kv_lo + K;
-                        float acc = 0.f;
-                        for (int c = lower_bound_i(s_sv, ncols, kk - Q); c < ncols && s_sv[c] <= kk + Q - 1; c = s_crun[c])
-                            acc += s_dvc[c * KV + (kk - (s_sv[c] - Q + 1))];
-                        slot[12 + it.ku_cap + K] = acc;
+#pragma unroll
+                    for (int o = 4; o >= 1; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+                    if (sl == 0 && kx < nkU + nkV) {
+                        const float val = zero ? 0.f : acc;
+                        if (kx < nkU) {
+                            if (single) kp.grad_knots[it.knot_u + kk] = val;
+                            else slot[12 + (kk - ku_lo)] = val;
+                        } else {
+                            if (single) kp.grad_knots[it.knot_v + kk] = val;
+                            else slot[12 + it.ku_cap + (kk - kv_lo)] = val;
+                        }
                     }
                 }
-                if (tid == 0) { sh[2] = kv_lo; sh[3] = nkv; }
+                if (tid == 0) { sh[0] = ku_lo; sh[1] = nku; sh[2] = kv_lo; sh[3] = nkv; }
             } else if (tid == 0) {
                 sh[0] = 0; sh[1] = 0; sh[2] = 0; sh[3] = 0;
             }
@@ -1004,7 +1034,7 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
         if (single) {
             // the only tile of its item: reduce its own units (shared memory or its slot)
             __syncthreads();
-            if (it.smemA) final_ctrl_smem(kp, tl.item, nwr, PB, s_flag + 32, jlo_t, cw_t);
+            if (it.smemA) final_ctrl_smem(kp, it, nwr, PB, s_flag + 32, jlo_t, cw_t, net_staged ? s_win : nullptr);
             else final_reduce(kp, tl.item, true);
         } else {
             // publish the partials (the barrier orders the CTA's writes before thread 0's

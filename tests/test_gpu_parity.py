@@ -29,8 +29,12 @@ def mixed_surfaces(seed, count=6):
 
 def curves_mixed(seed):
     rng = np.random.default_rng(seed)
-    specs = [(3, 64, 1024), (1, 2, 5), (2, 17, 300), (4, 9, 33), (5, 6, 1), (3, 100, 2049), (2, 3, 257)]
-    return [synth.curve(rng, p, n1, nu) for p, n1, nu in specs]
+    # (degree, control points, samples): the curve kernels take up to 256 control
+    # points, longer polygons go to the tile kernels; (2, 60, 4) jumps over spans
+    specs = [(3, 64, 1024), (1, 2, 5), (2, 17, 300), (4, 9, 33), (5, 6, 1), (3, 100, 2049), (2, 3, 257),
+             (3, 300, 700), (2, 60, 4), (5, 256, 3001), (1, 40, 129)]
+    # every knot gap >= 1e-3 is out of reach for hundreds of knots: scale the gap
+    return [synth.curve(rng, p, n1, nu, min_gap=min(1e-3, 0.01 / n1)) for p, n1, nu in specs]
 
 
 # ------------------------------------------------------------------- forward
@@ -277,8 +281,18 @@ def test_device_checks_flag_bad_inputs():
     _check_flag([unsorted], 5)
 
 
-def _check_flag(items, status):
-    pk = pack(items, SURF)
+def test_device_checks_flag_bad_curves():
+    rng = np.random.default_rng(15)
+    for n1, nu in ((20, 300), (300, 500)):          # curve kernels, then the tile kernels
+        c = synth.curve(rng, 3, n1, nu, min_gap=1e-5)
+        _check_flag([synth.Curve(c.p, c.U[::-1].copy(), c.ctrl, c.u)], 2, CURVE)
+        _check_flag([synth.Curve(c.p, c.U, c.ctrl, c.u * 1.5)], 4, CURVE)
+        _check_flag([synth.Curve(c.p, c.U, c.ctrl, c.u[::-1].copy())], 5, CURVE)
+
+
+def _check_flag(items, status, kind=None):
+    kind = SURF if kind is None else kind
+    pk = pack(items, kind)
     plan = batch.Plan.for_packed(pk)
     kn, ct, pr = batch.to_device(pk)
     pts = torch.zeros((pk.npts, 3), device="cuda")
