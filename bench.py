@@ -376,8 +376,7 @@ def bench_ragged(dev, steps, warmup, flush, peak, count=1000):
     _, tct, _ = batch.to_device(tk, dev)
     tpts = torch.empty((pk.npts, 3), device=dev)
     batch.Plan.for_packed(tk, device=dev).eval(kn, tct, pr, tpts)
-    eng = engine.RaggedEngine(surfs, tpts.cpu().numpy(), device=dev,
-                              candidates=[(4, 16), (4, 32), (4, 64), (2, 32)])
+    eng = engine.RaggedEngine(surfs, tpts.cpu().numpy(), device=dev)
     eng.capture()
     stream = torch.cuda.current_stream(dev)
     ms = _time_steps(eng.replay, steps, warmup, flush, stream)

@@ -46,14 +46,21 @@ class RaggedEngine:
         for k in keys:
             sel = np.nonzero((pk.descs["p"] == k[0]) & (pk.descs["q"] == k[1]))[0]
             sub = pk.descs[sel]
-            warps, rows = 4, 32
+            # CTA budget: this group's share of a full wave of CTA slots (a 128-register
+            # tile kernel fits 16 warps per SM), at least one SM's worth; tile shapes
+            # are tuned under that budget
+            share = work[k] / total
+
+            def budget(w, share=share):
+                per_sm = max(1, 16 // w)
+                return max(per_sm, int(round(share * sms * per_sm)))
+
+            warps, rows = 8, 128
             if autotune:
                 sub_packed = batch.Packed(pk.kind, sub, pk.knots, pk.ctrl, pk.params, pk.npts)
                 (warps, rows), _ = tune.autotune(sub_packed, self._tensors(), op="mse", candidates=candidates,
-                                                 reps=3, device=self.device)
-            # CTA budget: this group's share of a full wave (at least one SM's worth)
-            share = work[k] / total
-            max_ctas = max(4, int(round(share * sms * 4)))
+                                                 reps=3, device=self.device, max_ctas=budget)
+            max_ctas = budget(warps)
             plan = batch.Plan(pk.kind, sub, device=self.device, warps=warps, rows=rows, max_ctas=max_ctas)
             # loss_items is indexed by the plan's own item order: one buffer per group
             self.groups.append(dict(key=k, items=sel, plan=plan, tile=(warps, rows), max_ctas=max_ctas,
@@ -109,12 +116,17 @@ class RaggedEngine:
 
 
 class PerItemEngine:
-    """The same kernels, one plan and one launch per surface (the unbatched form)."""
+    """The same kernels, one plan and one launch per surface (the unbatched form),
+    each with the tile shape of its degree group in the batched engine."""
 
-    def __init__(self, eng: RaggedEngine, warps=4, rows=32):
+    def __init__(self, eng: RaggedEngine):
         self.eng = eng
         pk = eng.packed
-        self.plans = [batch.Plan(pk.kind, pk.descs[k: k + 1], device=eng.device, warps=warps, rows=rows)
+        tile = {}
+        for g in eng.groups:
+            for k in g["items"]:
+                tile[int(k)] = g["tile"]
+        self.plans = [batch.Plan(pk.kind, pk.descs[k: k + 1], device=eng.device, warps=tile[k][0], rows=tile[k][1])
                       for k in range(pk.count)]
 
     def step(self):

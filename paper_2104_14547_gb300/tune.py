@@ -38,20 +38,24 @@ def _time(fn, reps, flush):
 
 
 def autotune(packed: batch.Packed, tensors: dict, op: str = "mse", candidates=None, reps: int = 5,
-             device="cuda"):
+             device="cuda", max_ctas=None):
     """Return (best (warps, rows), {cfg: ms}) for `op` in {"eval", "mse", "backward"}.
 
     tensors holds the device arrays the op needs: knots, ctrl, params and, for
-    the gradient ops, target/grad_pts plus output buffers.
+    the gradient ops, target/grad_pts plus output buffers.  max_ctas, when
+    given, maps a warp count to the CTA cap each candidate is timed under (the
+    share of the GPU the plan will get when it runs beside others).
     """
-    key = signature(packed, op)
+    key = signature(packed, op) + ("" if max_ctas is None else repr([max_ctas(w) for w, _ in
+                                                                      (candidates or DEFAULT_CANDIDATES)]))
     if key in _cache:
         return _cache[key]
     cands = candidates or DEFAULT_CANDIDATES
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=device)
     table = {}
     for warps, rows in cands:
-        plan = batch.Plan.for_packed(packed, device=device, warps=warps, rows=rows)
+        cap = 0 if max_ctas is None else int(max_ctas(warps))
+        plan = batch.Plan.for_packed(packed, device=device, warps=warps, rows=rows, max_ctas=cap)
         kn, ct, pr = tensors["knots"], tensors["ctrl"], tensors["params"]
         if op == "eval":
             fn = lambda: plan.eval(kn, ct, pr, tensors["pts"])
