@@ -355,6 +355,118 @@ void nurbs_oracle_curve_vjp(int p, int n1, const double* U, const double* ctrl,
 }
 
 /* ---------------------------------------------------------------------------
+ * Parametric derivatives (the u-derivative of Eq. 4, for the surface tangents
+ * and normals the paper's offsetting application uses, Sec. 3.1 and Sec. 4).
+ *
+ * d/du N_i^p(u) = p N_i^{p-1}(u) / (U_{i+p} - U_i) - p N_{i+1}^{p-1}(u) / (U_{i+p+1} - U_{i+1}),
+ * a term with a zero denominator taken as 0.  The degree p-1 functions come from
+ * nurbs_oracle_basis_funs on the same span (those of other indices vanish on it).
+ * dN[r] = dN_{span-p+r}(u) / du, r = 0..p.
+ * ------------------------------------------------------------------------- */
+void nurbs_oracle_basis_ders(int span, double u, int p, const double* U, double* dN)
+{
+    if (p == 0) {
+        dN[0] = 0.0;
+        return;
+    }
+    double Nm1[OR_MAXDEG + 1];
+    nurbs_oracle_basis_funs(span, u, p - 1, U, Nm1);   /* N^{p-1}_{span-p+1 .. span} */
+    for (int r = 0; r <= p; ++r) {
+        int i = span - p + r;
+        double left = (r >= 1) ? Nm1[r - 1] : 0.0;    /* N^{p-1}_i */
+        double right = (r <= p - 1) ? Nm1[r] : 0.0;   /* N^{p-1}_{i+1} */
+        double d1 = U[i + p] - U[i], d2 = U[i + p + 1] - U[i + 1];
+        double a = (d1 != 0.0) ? p * left / d1 : 0.0;
+        double b = (d2 != 0.0) ? p * right / d2 : 0.0;
+        dN[r] = a - b;
+    }
+}
+
+/* Rational derivative of the quotient S = A / W: S' = (A' - W' S) / W. */
+static void rational_deriv(const double* A, double W, const double* Ad, double Wd, const double* S, double* out)
+{
+    for (int c = 0; c < 3; ++c) out[c] = (Ad[c] - Wd * S[c]) / W;
+    (void)A;
+}
+
+/* Surface points, tangents S_u, S_v and unit normals (S_u x S_v normalised; a zero
+ * cross product gives a zero normal).  Each output may be NULL; layout [a][b][3]. */
+void nurbs_oracle_surface_derivs(int p, int q, int n1, int m1, const double* U, const double* V,
+                                 const double* ctrl, int nu, const double* u, int nv, const double* v,
+                                 double* out_S, double* out_Su, double* out_Sv, double* out_N)
+{
+    for (int a = 0; a < nu; ++a) {
+        double Nu[OR_MAXDEG + 1], dNu[OR_MAXDEG + 1];
+        int su = nurbs_oracle_find_span(n1 - 1, p, u[a], U);
+        nurbs_oracle_basis_funs(su, u[a], p, U, Nu);
+        nurbs_oracle_basis_ders(su, u[a], p, U, dNu);
+        for (int b = 0; b < nv; ++b) {
+            double Nv[OR_MAXDEG + 1], dNv[OR_MAXDEG + 1];
+            int sv = nurbs_oracle_find_span(m1 - 1, q, v[b], V);
+            nurbs_oracle_basis_funs(sv, v[b], q, V, Nv);
+            nurbs_oracle_basis_ders(sv, v[b], q, V, dNv);
+            double A[3] = {0, 0, 0}, Au[3] = {0, 0, 0}, Av[3] = {0, 0, 0}, W = 0, Wu = 0, Wv = 0;
+            for (int r = 0; r <= p; ++r)
+                for (int h = 0; h <= q; ++h) {
+                    const double* c = ctrl + 4 * ((size_t)(su - p + r) * m1 + (sv - q + h));
+                    double w = c[3];
+                    for (int k = 0; k < 3; ++k) {
+                        A[k] += Nu[r] * Nv[h] * w * c[k];
+                        Au[k] += dNu[r] * Nv[h] * w * c[k];
+                        Av[k] += Nu[r] * dNv[h] * w * c[k];
+                    }
+                    W += Nu[r] * Nv[h] * w;
+                    Wu += dNu[r] * Nv[h] * w;
+                    Wv += Nu[r] * dNv[h] * w;
+                }
+            double S[3] = {A[0] / W, A[1] / W, A[2] / W}, Su[3], Sv[3];
+            rational_deriv(A, W, Au, Wu, S, Su);
+            rational_deriv(A, W, Av, Wv, S, Sv);
+            size_t o = 3 * ((size_t)a * nv + b);
+            for (int k = 0; k < 3; ++k) {
+                if (out_S) out_S[o + k] = S[k];
+                if (out_Su) out_Su[o + k] = Su[k];
+                if (out_Sv) out_Sv[o + k] = Sv[k];
+            }
+            if (out_N) {
+                double n[3] = {Su[1] * Sv[2] - Su[2] * Sv[1], Su[2] * Sv[0] - Su[0] * Sv[2],
+                               Su[0] * Sv[1] - Su[1] * Sv[0]};
+                double len = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+                for (int k = 0; k < 3; ++k) out_N[o + k] = len > 0.0 ? n[k] / len : 0.0;
+            }
+        }
+    }
+}
+
+/* Curve points and tangents C'(u); either output may be NULL; layout [a][3]. */
+void nurbs_oracle_curve_derivs(int p, int n1, const double* U, const double* ctrl, int nu, const double* u,
+                               double* out_C, double* out_Cu)
+{
+    for (int a = 0; a < nu; ++a) {
+        double N[OR_MAXDEG + 1], dN[OR_MAXDEG + 1];
+        int s = nurbs_oracle_find_span(n1 - 1, p, u[a], U);
+        nurbs_oracle_basis_funs(s, u[a], p, U, N);
+        nurbs_oracle_basis_ders(s, u[a], p, U, dN);
+        double A[3] = {0, 0, 0}, Ad[3] = {0, 0, 0}, W = 0, Wd = 0;
+        for (int r = 0; r <= p; ++r) {
+            const double* c = ctrl + 4 * (s - p + r);
+            for (int k = 0; k < 3; ++k) {
+                A[k] += N[r] * c[3] * c[k];
+                Ad[k] += dN[r] * c[3] * c[k];
+            }
+            W += N[r] * c[3];
+            Wd += dN[r] * c[3];
+        }
+        double C[3] = {A[0] / W, A[1] / W, A[2] / W}, Cu[3];
+        rational_deriv(A, W, Ad, Wd, C, Cu);
+        for (int k = 0; k < 3; ++k) {
+            if (out_C) out_C[3 * a + k] = C[k];
+            if (out_Cu) out_Cu[3 * a + k] = Cu[k];
+        }
+    }
+}
+
+/* ---------------------------------------------------------------------------
  * Mean squared error between evaluated points and a target (the L2 loss of
  * Sec. 4 read as a mean of squared coordinate differences):
  *   L = sum (S - T)^2 / count,  g = 2 (S - T) / count.

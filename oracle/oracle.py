@@ -12,6 +12,8 @@ inputs the GPU path sees) and calls the C routine of the same role:
 * ``basis_knot_jac``                  -- knot Jacobian of the nonzero basis (Sec. 3.2)
 * ``surface_eval`` / ``curve_eval``   -- Eq. 3 (and its one-direction form)
 * ``surface_vjp`` / ``curve_vjp``     -- Eq. 7, Eq. 8, Eq. 9 + knot derivative
+* ``basis_ders``                      -- u-derivative of the nonzero basis (of Eq. 4)
+* ``surface_derivs`` / ``curve_derivs`` -- tangents S_u, S_v, unit normals (curve: C')
 * ``mse``, ``adam``                   -- the L2 (MSE) loss and the Adam step of Sec. 4
 """
 from __future__ import annotations
@@ -59,6 +61,9 @@ def lib():
             L.nurbs_oracle_surface_vjp.argtypes = [i, i, i, i, _D, _D, _D, i, _D, i, _D, _D, _D, _D, _D]
             L.nurbs_oracle_curve_eval.argtypes = [i, i, _D, _D, i, _D, _D]
             L.nurbs_oracle_curve_vjp.argtypes = [i, i, _D, _D, i, _D, _D, _D, _D]
+            L.nurbs_oracle_basis_ders.argtypes = [i, d, i, _D, _D]
+            L.nurbs_oracle_surface_derivs.argtypes = [i, i, i, i, _D, _D, _D, i, _D, i, _D, _D, _D, _D, _D]
+            L.nurbs_oracle_curve_derivs.argtypes = [i, i, _D, _D, i, _D, _D, _D]
             L.nurbs_oracle_mse.argtypes = [sz, _D, _D, d, _D]
             L.nurbs_oracle_mse.restype = d
             L.nurbs_oracle_adam.argtypes = [sz, _D, _D, _D, _D, i, d, d, d, d]
@@ -149,6 +154,32 @@ def curve_vjp(p, U, ctrl, u, g, want_ctrl=True, want_knots=True):
 
 
 # ----------------------------------------------------------------- loss, adam
+
+def basis_ders(span: int, u: float, p: int, U) -> np.ndarray:
+    """dN_{span-p+r}(u)/du, r = 0..p (the u-derivative of Eq. 4)."""
+    U = _f64(U)
+    dN = np.zeros(p + 1)
+    lib().nurbs_oracle_basis_ders(span, float(u), p, _p(U), _p(dN))
+    return dN
+
+
+def surface_derivs(p, q, U, V, ctrl, u, v):
+    """Points, tangents S_u, S_v and unit normals, each [nu, nv, 3]."""
+    U, V, ctrl, u, v = _f64(U), _f64(V), _f64(ctrl), _f64(u), _f64(v)
+    n1, m1 = ctrl.shape[0], ctrl.shape[1]
+    outs = [np.zeros((len(u), len(v), 3)) for _ in range(4)]
+    lib().nurbs_oracle_surface_derivs(p, q, n1, m1, _p(U), _p(V), _p(ctrl), len(u), _p(u), len(v), _p(v),
+                                      *[_p(x) for x in outs])
+    return tuple(outs)
+
+
+def curve_derivs(p, U, ctrl, u):
+    """Points and tangents C'(u), each [nu, 3]."""
+    U, ctrl, u = _f64(U), _f64(ctrl), _f64(u)
+    C, Cu = np.zeros((len(u), 3)), np.zeros((len(u), 3))
+    lib().nurbs_oracle_curve_derivs(p, ctrl.shape[0], _p(U), _p(ctrl), len(u), _p(u), _p(C), _p(Cu))
+    return C, Cu
+
 def mse(S, T, count: float):
     """(L, g): L = sum (S-T)^2 / count, g = 2 (S-T) / count."""
     S, T = _f64(S), _f64(T)
