@@ -258,6 +258,8 @@ def run_ours(args):
     extras = {}
     if rank == 0 and not args.no_extra:
         extras["curves_fit_step"] = bench_curves(dev, max(5, args.steps // 2), args.warmup, flush, peak)
+        extras["tangents_normals"] = bench_derivs(dev, max(5, args.steps // 2), args.warmup, flush, peak, plan,
+                                                  kn, ct, pr, npts, pk.descs)
         extras["ragged_graph"] = bench_ragged(dev, max(5, args.steps // 2), args.warmup, flush, peak)
     if rank == 0 and args.serve:
         extras["serving"] = bench_serve(dev, n_requests=args.serve_requests)
@@ -359,6 +361,24 @@ def bench_curves(dev, steps, warmup, flush, peak):
     ach = abytes / (ms / 1e3) / 1e9
     return {"workload": "4096 cubic 3-D curves, 64 control points, 1024 samples, fused fit step (fwd + MSE + bwd + Adam)",
             "value": pk.npts / (ms / 1e3), "unit": "curve pts/s", "ms_per_step": ms,
+            "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                         "algorithmic_bytes": abytes}}
+
+
+def bench_derivs(dev, steps, warmup, flush, peak, plan, kn, ct, pr, npts, descs):
+    """The bench batch evaluated with tangents and unit normals (points, S_u, S_v,
+    normals written: 48 B per point)."""
+    import torch
+    outs = [torch.empty((npts, 3), device=dev) for _ in range(4)]
+    stream = torch.cuda.current_stream(dev)
+    ms = _time_steps(lambda: plan.eval_derivs(kn, ct, pr, *outs), steps, warmup, flush, stream)
+    abytes = 48 * npts
+    for d in descs:
+        nc = int(d["n1"]) * int(d["m1"])
+        abytes += 16 * nc + 4 * (int(d["n1"] + d["p"] + 1) + int(d["m1"] + d["q"] + 1)) + 4 * (int(d["nu"]) + int(d["nv"]))
+    ach = abytes / (ms / 1e3) / 1e9
+    return {"workload": "the bench batch, forward with tangents S_u, S_v and unit normals",
+            "value": npts / (ms / 1e3), "unit": "surface pts/s", "ms_per_step": ms,
             "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
                          "algorithmic_bytes": abytes}}
 

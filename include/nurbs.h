@@ -149,6 +149,32 @@ nurbs_status nurbs_eval_curve(const nurbs_plan* plan, const float* knots, const 
                               const float* params, float* pts, nurbs_stream_t stream);
 
 /*
+ * nurbs_eval_surface_derivs -- forward evaluation with the surface tangents and
+ * unit normals that the paper's surface-offsetting application needs (the
+ * derivatives S_,u and S_,v of Sec. 3.2; offsetting in Sec. 4).
+ *   Tangents: S_u = (A_u - W_u S) / W, where S' = (A, W) is the homogeneous point
+ *   of Eq. 3 and A_u, W_u take the u-derivative of the basis (of Eq. 4) in place
+ *   of the basis.  S_v is defined the same way.
+ *   Normals: S_u x S_v / |S_u x S_v|; a degenerate point (zero cross product)
+ *   gets 0.
+ * pts, du, dv, normals: device arrays in the points' layout ([npts][3] floats at
+ * each item's pts offset).  Any of them may be NULL, but not all.  Samples on a
+ * knot see the derivative from the right, except at the end of the domain.
+ * Errors: as nurbs_eval_surface; NURBS_ERR_ARG when every output is NULL.
+ */
+nurbs_status nurbs_eval_surface_derivs(const nurbs_plan* plan, const float* knots, const float* ctrl,
+                                       const float* params, float* pts, float* du, float* dv, float* normals,
+                                       nurbs_stream_t stream);
+
+/*
+ * nurbs_eval_curve_derivs -- curve points and tangents C'(u) = (A' - W' C) / W
+ * (the curve form of nurbs_eval_surface_derivs).  pts and tangents are device
+ * arrays in the points' layout.  Either may be NULL, but not both.
+ */
+nurbs_status nurbs_eval_curve_derivs(const nurbs_plan* plan, const float* knots, const float* ctrl,
+                                     const float* params, float* pts, float* tangents, nurbs_stream_t stream);
+
+/*
  * nurbs_backward -- vector-Jacobian product of the evaluation (Sec. 3.2, Eq. 7,
  * Eq. 8, Eq. 9, the knot derivative, Alg. 2), for surface or curve plans.
  *   grad_pts    dL/dS in the pts layout

@@ -108,6 +108,8 @@ SIGNATURES = {
     "nurbs_plan_get_error": (_i32, [_vp, _vp, ctypes.POINTER(ctypes.c_uint32)]),
     "nurbs_eval_surface": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "nurbs_eval_curve": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    "nurbs_eval_surface_derivs": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "nurbs_eval_curve_derivs": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "nurbs_backward": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "nurbs_mse_fwd_bwd": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _f, _vp]),
     "nurbs_mse_fwd_bwd_noalloc": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _f, _vp]),

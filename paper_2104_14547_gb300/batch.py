@@ -170,6 +170,19 @@ class Plan:
         _lib.check(fn(self.handle, _ptr(knots), _ptr(ctrl), _ptr(params), _ptr(pts), _stream(stream)), fn.__name__)
         return pts
 
+    def eval_derivs(self, knots, ctrl, params, pts=None, du=None, dv=None, normals=None, stream=None):
+        """Points with tangents and unit normals (surfaces: du, dv, normals; curves:
+        the tangent goes to ``du``).  Outputs that are None are not written."""
+        if self.kind == _lib.KIND_CURVE:
+            _lib.check(self.lib.nurbs_eval_curve_derivs(self.handle, _ptr(knots), _ptr(ctrl), _ptr(params),
+                                                        _ptr(pts), _ptr(du), _stream(stream)),
+                       "nurbs_eval_curve_derivs")
+        else:
+            _lib.check(self.lib.nurbs_eval_surface_derivs(self.handle, _ptr(knots), _ptr(ctrl), _ptr(params),
+                                                          _ptr(pts), _ptr(du), _ptr(dv), _ptr(normals),
+                                                          _stream(stream)), "nurbs_eval_surface_derivs")
+        return pts, du, dv, normals
+
     def backward(self, knots, ctrl, params, grad_pts, grad_ctrl=None, grad_knots=None, stream=None):
         _lib.check(self.lib.nurbs_backward(self.handle, _ptr(knots), _ptr(ctrl), _ptr(params), _ptr(grad_pts),
                                            _ptr(grad_ctrl), _ptr(grad_knots), _stream(stream)), "nurbs_backward")

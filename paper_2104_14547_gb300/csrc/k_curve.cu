@@ -4,16 +4,16 @@
 
 namespace nurbs {
 
-template <int P, bool G, bool K, bool M>
+template <int P, bool G, bool K, bool M, bool D = false>
 struct CurveVariantOf {
     static cudaError_t launch(const KParams& kp, int grid, int block, int smem, cudaStream_t s)
     {
-        curves_kernel<P, G, K, M><<<grid, block, smem, s>>>(kp);
+        curves_kernel<P, G, K, M, D><<<grid, block, smem, s>>>(kp);
         return cudaGetLastError();
     }
     static cudaError_t occupancy(int* n, int block, int smem)
     {
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, curves_kernel<P, G, K, M>, block, smem);
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, curves_kernel<P, G, K, M, D>, block, smem);
     }
     static cudaError_t set_smem(int* limit)
     {
@@ -21,10 +21,10 @@ struct CurveVariantOf {
         cudaFuncAttributes fa;
         cudaError_t e = cudaGetDevice(&dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-        if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, curves_kernel<P, G, K, M>);
+        if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, curves_kernel<P, G, K, M, D>);
         if (e != cudaSuccess) return e;
         *limit = optin - (int)fa.sharedSizeBytes;
-        return cudaFuncSetAttribute(curves_kernel<P, G, K, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, *limit);
+        return cudaFuncSetAttribute(curves_kernel<P, G, K, M, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, *limit);
     }
     static KernelVariant get() { return KernelVariant{launch, occupancy, set_smem}; }
 };
@@ -37,7 +37,8 @@ static KernelVariant pick(int v)
         case 1: return CurveVariantOf<P, true, false, false>::get();
         case 2: return CurveVariantOf<P, true, true, false>::get();
         case 3: return CurveVariantOf<P, true, false, true>::get();
-        default: return CurveVariantOf<P, true, true, true>::get();
+        case 4: return CurveVariantOf<P, true, true, true>::get();
+        default: return CurveVariantOf<P, false, false, false, true>::get();
     }
 }
 

@@ -11,7 +11,8 @@ static KernelVariant pick(int v)
         case 1: return VariantOf<5, Q, true, false, false>::get();
         case 2: return VariantOf<5, Q, true, true, false>::get();
         case 3: return VariantOf<5, Q, true, false, true>::get();
-        default: return VariantOf<5, Q, true, true, true>::get();
+        case 4: return VariantOf<5, Q, true, true, true>::get();
+        default: return VariantOf<5, Q, false, false, false, true>::get();
     }
 }
 

@@ -40,7 +40,7 @@ struct PlanGroup {
     int p, q;         // internal degrees (p == 0 for curves)
     int ck;           // 1: curve-kernel group (degree q, one warp per curve)
     int t0, t1;       // tile range
-    int grid[5];      // CTAs per launch of each kernel variant (0 = unknown)
+    int grid[6];      // CTAs per launch of each kernel variant (0 = unknown)
 };
 
 struct nurbs_plan {
@@ -54,7 +54,7 @@ struct nurbs_plan {
     // shared memory carve-up
     int R, C, acc_cap;
     int off_misc, off_su, off_u, off_nu, off_sv, off_v, off_nv, off_stage, off_beta, off_duc, off_dvc, off_ring,
-        off_jb, off_win, off_run, off_knots, off_w, off_acc, off_sa;
+        off_jb, off_win, off_run, off_knots, off_w, off_acc, off_sa, off_dnu;
     int smem_bytes;           // gradient kernels
     int smem_eval;            // forward kernels (no shared adjoint)
     int c_mc, c_wbytes, c_smem;   // curve kernels: control capacity, bytes per warp, per CTA
@@ -158,7 +158,7 @@ nurbs_status nurbs_plan_create(int32_t kind, const nurbs_desc* h_desc, int32_t c
         PlanGroup grp;
         grp.p = 0; grp.q = q; grp.ck = 1;
         grp.t0 = (int)pl->tiles.size();
-        for (int v = 0; v < 5; ++v) grp.grid[v] = 0;
+        for (int v = 0; v < 6; ++v) grp.grid[v] = 0;
         for (int32_t k = 0; k < count; ++k) {
             ItemDev& it = pl->items[k];
             if (!it.ck || it.q != q) continue;
@@ -184,7 +184,7 @@ nurbs_status nurbs_plan_create(int32_t kind, const nurbs_desc* h_desc, int32_t c
         PlanGroup grp;
         grp.p = gp; grp.q = gq; grp.ck = 0;
         grp.t0 = (int)pl->tiles.size();
-        for (int v = 0; v < 5; ++v) grp.grid[v] = 0;
+        for (int v = 0; v < 6; ++v) grp.grid[v] = 0;
         for (int32_t k = 0; k < count; ++k) {
             ItemDev& it = pl->items[k];
             if (it.p != gp || it.q != gq || it.ck) continue;
@@ -271,6 +271,7 @@ nurbs_status nurbs_plan_create(int32_t kind, const nurbs_desc* h_desc, int32_t c
         max_knots = std::max(max_knots, align4(it.n1 + it.p + 1) + it.m1 + it.q + 1);
     pl->off_knots = take(4 * max_knots);
     pl->off_w = take(4 * (kJbCap + maxC * sv));
+    pl->off_dnu = take(4 * maxR * su);   // row basis derivatives (forward with tangents)
     size_t sa_bytes = 0;
     for (const ItemDev& it : pl->items)
         if (it.smemA) sa_bytes = std::max(sa_bytes, smem_adjoint_bytes(it, pl->tiles[it.first_tile].nwr));
@@ -364,7 +365,7 @@ GroupLaunch group_launch(const nurbs_plan* pl, const PlanGroup& grp, int v)
 {
     if (grp.ck)
         return GroupLaunch{curve_variant(v, grp.q), 32 * kCurveWarps, pl->c_smem, kMaxGroups + grp.q - 1, kCurveWarps};
-    return GroupLaunch{variant_for(v, grp.p, grp.q), 32 * pl->warps, v == 0 ? pl->smem_eval : pl->smem_bytes,
+    return GroupLaunch{variant_for(v, grp.p, grp.q), 32 * pl->warps, (v == 0 || v == 5) ? pl->smem_eval : pl->smem_bytes,
                        grp.p * 5 + grp.q - 1, 1};
 }
 
@@ -409,6 +410,7 @@ void fill_tables(KParams& kp, const nurbs_plan* pl, unsigned char* ws)
     kp.off_beta = pl->off_beta; kp.off_duc = pl->off_duc; kp.off_dvc = pl->off_dvc; kp.off_ring = pl->off_ring;
     kp.off_jb = pl->off_jb; kp.off_win = pl->off_win; kp.off_run = pl->off_run;
     kp.off_knots = pl->off_knots; kp.off_w = pl->off_w; kp.off_sa = pl->off_sa; kp.off_acc = pl->off_acc;
+    kp.off_dnu = pl->off_dnu;
     kp.acc_cap = pl->acc_cap;
     kp.c_mc = pl->c_mc;
     kp.c_wbytes = pl->c_wbytes;
@@ -453,7 +455,7 @@ int32_t nurbs_plan_ctas(const nurbs_plan* plan)
 {
     if (plan == nullptr) return 0;
     int n = 0;
-    for (const PlanGroup& g : plan->groups) n += *std::max_element(g.grid, g.grid + 5);
+    for (const PlanGroup& g : plan->groups) n += *std::max_element(g.grid, g.grid + 6);
     return n;
 }
 
@@ -484,6 +486,42 @@ nurbs_status nurbs_eval_curve(const nurbs_plan* plan, const float* knots, const 
                               const float* params, float* pts, nurbs_stream_t stream)
 {
     return eval_common(plan, NURBS_KIND_CURVE, knots, ctrl, params, pts, stream);
+}
+
+static nurbs_status derivs_common(const nurbs_plan* pl, int32_t kind, const float* knots, const float* ctrl,
+                                  const float* params, float* pts, float* du, float* dv, float* normals,
+                                  nurbs_stream_t stream)
+{
+    if (pl == nullptr) return NURBS_ERR_ARG;
+    if (pl->kind != kind) return NURBS_ERR_KIND;
+    if (pl->tiles.empty()) return NURBS_OK;
+    if (knots == nullptr || ctrl == nullptr || params == nullptr) return NURBS_ERR_ARG;
+    if (pts == nullptr && du == nullptr && dv == nullptr && normals == nullptr) return NURBS_ERR_ARG;
+    if (((uintptr_t)ctrl & 15u) != 0) return NURBS_ERR_ARG;
+    KParams kp;
+    zero_params(kp);
+    kp.knots = knots;
+    kp.ctrl = reinterpret_cast<const float4*>(ctrl);
+    kp.params = params;
+    kp.pts = pts;
+    kp.d_du = du;
+    kp.d_dv = dv;
+    kp.d_nrm = normals;
+    return launch(pl, 5, kp, reinterpret_cast<cudaStream_t>(stream));
+}
+
+nurbs_status nurbs_eval_surface_derivs(const nurbs_plan* plan, const float* knots, const float* ctrl,
+                                       const float* params, float* pts, float* du, float* dv, float* normals,
+                                       nurbs_stream_t stream)
+{
+    return derivs_common(plan, NURBS_KIND_SURFACE, knots, ctrl, params, pts, du, dv, normals, stream);
+}
+
+nurbs_status nurbs_eval_curve_derivs(const nurbs_plan* plan, const float* knots, const float* ctrl,
+                                     const float* params, float* pts, float* tangents, nurbs_stream_t stream)
+{
+    // a curve runs as the v direction of its item: its tangent is the v-derivative
+    return derivs_common(plan, NURBS_KIND_CURVE, knots, ctrl, params, pts, nullptr, tangents, nullptr, stream);
 }
 
 static nurbs_status grad_common(const nurbs_plan* pl, const float* knots, const float* ctrl, float* ctrl_w,

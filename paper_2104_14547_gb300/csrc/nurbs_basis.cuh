@@ -55,6 +55,43 @@ __device__ __forceinline__ void basis_funs(int s, float u, const float* U, float
     }
 }
 
+// The P+1 nonzero basis functions and their first u-derivatives on span s:
+// the triangle of basis_funs up to degree P-1 is kept, and
+//   dN_i^P / du = P N_i^{P-1} / (U_{i+P} - U_i) - P N_{i+1}^{P-1} / (U_{i+P+1} - U_{i+1})
+// (the u-derivative of Eq. 4; both denominators are positive on a non-empty span).
+template <int P>
+__device__ __forceinline__ void basis_funs_d(int s, float u, const float* U, float (&N)[P + 1], float (&dN)[P + 1])
+{
+    N[0] = 1.f;
+    dN[0] = 0.f;
+    if constexpr (P > 0) {
+        float left[P + 1], right[P + 1], prev[P + 1];
+#pragma unroll
+        for (int j = 1; j <= P; ++j) {
+            left[j] = u - U[s + 1 - j];
+            right[j] = U[s + j] - u;
+            if (j == P) {
+#pragma unroll
+                for (int r = 0; r < P; ++r) prev[r] = N[r];   // N^{P-1}_{s-P+1+r}
+            }
+            float saved = 0.f;
+#pragma unroll
+            for (int r = 0; r < j; ++r) {
+                float temp = N[r] * frcp(right[r + 1] + left[j - r]);
+                N[r] = fmaf(right[r + 1], temp, saved);
+                saved = left[j - r] * temp;
+            }
+            N[j] = saved;
+        }
+#pragma unroll
+        for (int r = 0; r <= P; ++r) {
+            const float a = r >= 1 ? prev[r - 1] * frcp(U[s + r] - U[s - P + r]) : 0.f;
+            const float b = r <= P - 1 ? prev[r] * frcp(U[s + r + 1] - U[s - P + r + 1]) : 0.f;
+            dN[r] = (float)P * (a - b);
+        }
+    }
+}
+
 // Reverse-mode derivative of basis_funs with respect to the knots (the knot
 // derivative of Sec. 3.2 in its sigma -> 0 reading: the degree-0 indicators
 // contribute nothing, every coefficient of Eq. 4 is differentiated).

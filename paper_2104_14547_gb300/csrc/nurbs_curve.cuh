@@ -51,7 +51,7 @@ __host__ __device__ constexpr int curve_off_ring(int mc, int P)
 }
 __host__ __device__ constexpr int curve_warp_bytes(int mc, int P) { return curve_off_ring(mc, P) + 2 * 32 * 16 * 4; }
 
-template <int P, bool GRAD, bool KNOTS, bool MSE>
+template <int P, bool GRAD, bool KNOTS, bool MSE, bool DER = false>
 __device__ __forceinline__ void curve_body(const KParams& kp, int t, unsigned char* wsm)
 {
     constexpr int PB = P + 1;
@@ -195,7 +195,9 @@ __device__ __forceinline__ void curve_body(const KParams& kp, int t, unsigned ch
         if (s < n && !(u < s_kn[s + 1])) s = find_span(n, P, u, s_kn);
         advance(s);
         float N[PB];
-        basis_funs<P>(s, u, s_kn, N);
+        float dN[DER ? PB : 1];
+        if constexpr (DER) basis_funs_d<P>(s, u, s_kn, N, dN);
+        else basis_funs<P>(s, u, s_kn, N);
         float4 Cw = f4zero();
 #pragma unroll
         for (int r = 0; r < PB; ++r) Cw = fma4(N[r], Qw[r], Cw);
@@ -204,6 +206,18 @@ __device__ __forceinline__ void curve_body(const KParams& kp, int t, unsigned ch
         if (has_pts) {
             float* o = kp.pts + 3 * (it.pts + b);
             o[0] = Sx; o[1] = Sy; o[2] = Sz;
+        }
+        if constexpr (DER) {
+            // tangent C' = (A' - W' C) / W with (A', W') = sum_r dN_r Pw_r
+            if (kp.d_dv != nullptr) {
+                float4 Cd = f4zero();
+#pragma unroll
+                for (int r = 0; r < PB; ++r) Cd = fma4(dN[r], Qw[r], Cd);
+                float* o = kp.d_dv + 3 * (it.pts + b);
+                o[0] = (Cd.x - Cd.w * Sx) * inv;
+                o[1] = (Cd.y - Cd.w * Sy) * inv;
+                o[2] = (Cd.z - Cd.w * Sz) * inv;
+            }
         }
         if constexpr (GRAD) {
             float ginv = inv;
@@ -340,7 +354,7 @@ __device__ __forceinline__ void curve_body(const KParams& kp, int t, unsigned ch
     __syncwarp();
 }
 
-template <int P, bool GRAD, bool KNOTS, bool MSE>
+template <int P, bool GRAD, bool KNOTS, bool MSE, bool DER = false>
 __global__ void __launch_bounds__(32 * kCurveWarps, 4) curves_kernel(const __grid_constant__ KParams kp)
 {
     extern __shared__ float4 smem4[];
@@ -349,7 +363,7 @@ __global__ void __launch_bounds__(32 * kCurveWarps, 4) curves_kernel(const __gri
     // the first curve of each warp is its own index; later ones come from the queue
     int t = kp.t0 + (int)blockIdx.x * kCurveWarps + warp;
     while (t < kp.t1) {
-        curve_body<P, GRAD, KNOTS, MSE>(kp, t, wsm);
+        curve_body<P, GRAD, KNOTS, MSE, DER>(kp, t, wsm);
         int nt = 0;
         if (lane == 0) nt = kp.t0 + (int)gridDim.x * kCurveWarps + (int)atomicAdd(kp.queue, 1u);
         t = __shfl_sync(0xffffffffu, nt, 0);

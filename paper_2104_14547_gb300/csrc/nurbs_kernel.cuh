@@ -5,14 +5,14 @@
 
 namespace nurbs {
 
-template <int P, int Q, bool GRAD, bool KNOTS, bool MSE>
+template <int P, int Q, bool GRAD, bool KNOTS, bool MSE, bool DER = false>
 __global__ void __launch_bounds__(256, 2) tiles_kernel(const __grid_constant__ KParams kp)
 {
     // the first tile of each CTA is its own index; later ones come from the queue
     __shared__ int s_t;
     int t = kp.t0 + (int)blockIdx.x;
     while (t < kp.t1) {
-        tile_body<P, Q, GRAD, KNOTS, MSE>(kp, t);
+        tile_body<P, Q, GRAD, KNOTS, MSE, DER>(kp, t);
         if (threadIdx.x == 0) s_t = kp.t0 + (int)gridDim.x + (int)atomicAdd(kp.queue, 1u);
         __syncthreads();
         t = s_t;
@@ -37,16 +37,16 @@ struct KernelVariant {
     cudaError_t (*set_smem)(int* limit);
 };
 
-template <int P, int Q, bool G, bool K, bool M>
+template <int P, int Q, bool G, bool K, bool M, bool D = false>
 struct VariantOf {
     static cudaError_t launch(const KParams& kp, int grid, int block, int smem, cudaStream_t s)
     {
-        tiles_kernel<P, Q, G, K, M><<<grid, block, smem, s>>>(kp);
+        tiles_kernel<P, Q, G, K, M, D><<<grid, block, smem, s>>>(kp);
         return cudaGetLastError();
     }
     static cudaError_t occupancy(int* n, int block, int smem)
     {
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, tiles_kernel<P, Q, G, K, M>, block, smem);
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, tiles_kernel<P, Q, G, K, M, D>, block, smem);
     }
     // Raise the kernel's dynamic shared-memory limit to what the device allows next to
     // its static shared memory (the attribute is per function, so it is never lowered).
@@ -56,16 +56,16 @@ struct VariantOf {
         cudaFuncAttributes fa;
         cudaError_t e = cudaGetDevice(&dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-        if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, tiles_kernel<P, Q, G, K, M>);
+        if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, tiles_kernel<P, Q, G, K, M, D>);
         if (e != cudaSuccess) return e;
         *limit = optin - (int)fa.sharedSizeBytes;
-        return cudaFuncSetAttribute(tiles_kernel<P, Q, G, K, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, *limit);
+        return cudaFuncSetAttribute(tiles_kernel<P, Q, G, K, M, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, *limit);
     }
     static KernelVariant get() { return KernelVariant{launch, occupancy, set_smem}; }
 };
 
 // variant: 0 forward; 1 / 2 backward from dL/dS without / with knot gradients;
-// 3 / 4 the same from an MSE target.
+// 3 / 4 the same from an MSE target; 5 forward with tangents and normals.
 // Defined per u degree in k_p<P>.cu.
 KernelVariant variant_p0(int v, int q);
 KernelVariant variant_p1(int v, int q);

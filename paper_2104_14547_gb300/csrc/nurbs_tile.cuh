@@ -70,9 +70,12 @@ struct KParams {
     // shared-memory carve-up in bytes (host-computed for the plan's largest tile)
     int R, C;
     int off_misc, off_su, off_u, off_nu, off_sv, off_v, off_nv, off_stage, off_beta, off_duc, off_dvc, off_ring,
-        off_jb, off_win, off_run, off_knots, off_w, off_acc, off_sa;
+        off_jb, off_win, off_run, off_knots, off_w, off_acc, off_sa, off_dnu;
 
     int acc_cap;             // bytes available to the final reduction from off_acc
+    float* d_du;             // forward with tangents: S_u, S_v, unit normals (each may be null)
+    float* d_dv;
+    float* d_nrm;
     int c_mc, c_wbytes;      // curve kernels: control-point capacity, shared bytes per warp
 };
 
@@ -411,7 +414,7 @@ static __device__ __noinline__ void final_reduce(const KParams& kp, int item, bo
 // partials; the last CTA of the item reduces them.  KNOTS adds beta / Gamma and
 // the knot partials.
 // ---------------------------------------------------------------------------
-template <int P, int Q, bool GRAD, bool KNOTS, bool MSE>
+template <int P, int Q, bool GRAD, bool KNOTS, bool MSE, bool DER = false>
 __device__ __forceinline__ void tile_body(const KParams& kp, int t)
 {
     extern __shared__ float4 smem4[];
@@ -540,7 +543,15 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
                     uc = fminf(fmaxf(u0, ulo), uhi);
                     s = find_span(n, P, uc, s_knU);
                 }
-                basis_funs<P>(s, uc, s_knU, N);
+                if constexpr (DER) {
+                    float dN[PB];
+                    basis_funs_d<P>(s, uc, s_knU, N, dN);
+                    float* s_dnu = reinterpret_cast<float*>(smem + kp.off_dnu);
+#pragma unroll
+                    for (int k = 0; k < PB; ++k) s_dnu[r * SU + k] = dN[k];
+                } else {
+                    basis_funs<P>(s, uc, s_knU, N);
+                }
                 s_su[r] = s;
 #pragma unroll
                 for (int k = 0; k < PB; ++k) s_nu[r * SU + k] = N[k];
@@ -666,6 +677,11 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
         float Nv[QB];
 #pragma unroll
         for (int h = 0; h < QB; ++h) Nv[h] = s_nv[blc * SV + h];
+        float dNv[DER ? QB : 1];   // tangents: the column's v-derivatives of its basis
+        if constexpr (DER) {
+            float nv_[QB];
+            basis_funs_d<Q>(svb, vb, s_knV, nv_, dNv);
+        }
         const float4* __restrict__ cbase = kp.ctrl + it.ctrl + (svb - Q);  // column of h = 0
         const int m1 = it.m1;
 
@@ -688,6 +704,23 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
                 const float4* cr = cbase + i * m1;
 #pragma unroll
                 for (int h = 0; h < QB; ++h) add(Nv[h], __ldg(cr + h));
+            }
+            return acc;
+        };
+
+        // tangents: Qv = sum_h dNv_h (w x, w y, w z, w) of row i's Q+1 control points
+        auto computeQv = [&](int i) -> float4 {
+            float4 acc = f4zero();
+            if constexpr (DER) {
+#pragma unroll
+                for (int h = 0; h < QB; ++h) {
+                    const float4 c = win ? (wbase + i * w_stride)[h] : __ldg(cbase + i * m1 + h);
+                    const float wn = dNv[h] * c.w;
+                    acc.x = fmaf(wn, c.x, acc.x);
+                    acc.y = fmaf(wn, c.y, acc.y);
+                    acc.z = fmaf(wn, c.z, acc.z);
+                    acc.w += wn;
+                }
             }
             return acc;
         };
@@ -762,6 +795,7 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
 
         float4 Qw[PB];
         float4 tau[PB];
+        float4 Qv[DER ? PB : 1];
         int cur = -1;
         // Move the window to u-span s: rows leave in increasing order (GRAD: retire them).
         auto advance = [&](int s) {
@@ -775,6 +809,10 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
                 }
 #pragma unroll
                 for (int k = 0; k < PB; ++k) { Qw[k] = computeQ(s - P + k); tau[k] = f4zero(); }
+                if constexpr (DER) {
+#pragma unroll
+                    for (int k = 0; k < PB; ++k) Qv[k] = computeQv(s - P + k);
+                }
                 cur = s;
             } else {
                 while (cur < s) {
@@ -784,6 +822,11 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
                     ++cur;
                     Qw[P] = computeQ(cur);
                     tau[P] = f4zero();
+                    if constexpr (DER) {
+#pragma unroll
+                        for (int k = 0; k < P; ++k) Qv[k] = Qv[k + 1];
+                        Qv[P] = computeQv(cur);
+                    }
                 }
             }
         };
@@ -792,6 +835,8 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
         const bool store = cvalid && kp.pts != nullptr;
         const bool full = nvw == 32;   // every lane of the warp holds a valid column
         float* orow = kp.pts != nullptr ? kp.pts + 3 * (prow0 + lane) : nullptr;   // row 0 of this lane
+        // derivative outputs share the points' layout: element offset of row 0 of this lane
+        const long long doff = 3 * (prow0 + lane);
         float* s_beta_w = reinterpret_cast<float*>(smem + kp.off_beta) + (wc * kp.R) * SU;
 
         // One or two rows (same u-span) per step: S, dL/dS, lambda, tau and beta.
@@ -819,6 +864,44 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
                 for (int q = 0; q < NR; ++q) {
                     float* o = orow + (r + q) * rstride;
                     if (store) { o[0] = Sx[q]; o[1] = Sy[q]; o[2] = Sz[q]; }
+                }
+                if constexpr (DER) {
+                    // S_u = (A_u - W_u S) / W with (A_u, W_u) = sum_r dNu_r Qw_r; S_v alike
+                    // with the dNv-contracted window; unit normal S_u x S_v / |S_u x S_v|
+                    const float* s_dnu = reinterpret_cast<const float*>(smem + kp.off_dnu);
+#pragma unroll
+                    for (int q = 0; q < NR; ++q) {
+                        float dNu[PB];
+                        load_basis<PB>(s_dnu + (r + q) * SU, dNu);
+                        float4 Au = f4zero(), Av = f4zero();
+#pragma unroll
+                        for (int k = 0; k < PB; ++k) {
+                            Au = fma4(dNu[k], Qw[k], Au);
+                            Av = fma4(Nu[q][k], Qv[k], Av);
+                        }
+                        const float ux = (Au.x - Au.w * Sx[q]) * inv[q], uy = (Au.y - Au.w * Sy[q]) * inv[q],
+                                    uz = (Au.z - Au.w * Sz[q]) * inv[q];
+                        const float vx = (Av.x - Av.w * Sx[q]) * inv[q], vy = (Av.y - Av.w * Sy[q]) * inv[q],
+                                    vz = (Av.z - Av.w * Sz[q]) * inv[q];
+                        if (cvalid) {
+                            const long long off = doff + (long long)(r + q) * rstride;
+                            if (kp.d_du != nullptr) {
+                                float* o = kp.d_du + off;
+                                o[0] = ux; o[1] = uy; o[2] = uz;
+                            }
+                            if (kp.d_dv != nullptr) {
+                                float* o = kp.d_dv + off;
+                                o[0] = vx; o[1] = vy; o[2] = vz;
+                            }
+                            if (kp.d_nrm != nullptr) {
+                                const float nx = uy * vz - uz * vy, ny = uz * vx - ux * vz, nz = ux * vy - uy * vx;
+                                const float l2 = fmaf(nx, nx, fmaf(ny, ny, nz * nz));
+                                const float il = l2 > 0.f ? rsqrtf(l2) : 0.f;
+                                float* o = kp.d_nrm + off;
+                                o[0] = nx * il; o[1] = ny * il; o[2] = nz * il;
+                            }
+                        }
+                    }
                 }
             } else {
                 if constexpr (NR == 2) cp_async_wait<kRing - 2>(); else cp_async_wait<kRing - 1>();
