@@ -261,6 +261,7 @@ def run_ours(args):
         extras["tangents_normals"] = bench_derivs(dev, max(5, args.steps // 2), args.warmup, flush, peak, plan,
                                                   kn, ct, pr, npts, pk.descs)
         extras["ragged_graph"] = bench_ragged(dev, max(5, args.steps // 2), args.warmup, flush, peak)
+        extras["offset_fit"] = bench_offset(dev, max(5, args.steps // 2), args.warmup, flush, peak)
     if rank == 0 and args.serve:
         extras["serving"] = bench_serve(dev, n_requests=args.serve_requests)
 
@@ -379,6 +380,33 @@ def bench_derivs(dev, steps, warmup, flush, peak, plan, kn, ct, pr, npts, descs)
     ach = abytes / (ms / 1e3) / 1e9
     return {"workload": "the bench batch, forward with tangents S_u, S_v and unit normals",
             "value": npts / (ms / 1e3), "unit": "surface pts/s", "ms_per_step": ms,
+            "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                         "algorithmic_bytes": abytes}}
+
+
+def bench_offset(dev, steps, warmup, flush, peak, count=4096):
+    """Surface offsetting (Sec. 4) on a batch of bicubic double-curved patches
+    (12x12 nets, 20x20 samples): targets from the GPU normals, then fused fit
+    steps toward them; time per fit step and the deviation reached."""
+    import torch
+    from paper_2104_14547_gb300 import offset, synth
+    surfs = synth.offset_batch(0, count)
+    d = 0.02
+    fit = offset.OffsetFit(surfs, d, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    ms = _time_steps(lambda: fit.step(2e-3), steps, warmup, flush, stream)
+    fit.run(max(0, 300 - fit.steps), 2e-3)
+    dev_fit = float(fit.deviation().max())
+    dev_cp = float(fit.control_point_offset_deviation().max())
+    npts = fit.packed.npts
+    nctrl = int((fit.packed.descs["n1"] * fit.packed.descs["m1"]).sum())
+    abytes = 12 * npts + nctrl * (16 * 2 + 32 * 2) + 4 * (len(fit.packed.knots) + len(fit.packed.params)) + 4 * count
+    ach = abytes / (ms / 1e3) / 1e9
+    return {"workload": f"{count} bicubic double-curved patches, 12x12 nets, 20x20 samples, offset d = {d}: "
+                        "fused fit step toward the offset points",
+            "value": npts / (ms / 1e3), "unit": "surface pts/s", "ms_per_step": ms,
+            "max_deviation_over_d_after_300_steps": dev_fit / d,
+            "control_point_offset_max_deviation_over_d": dev_cp / d,
             "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
                          "algorithmic_bytes": abytes}}
 

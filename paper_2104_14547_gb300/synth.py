@@ -171,3 +171,28 @@ def ragged_batch(seed: int = 0, batch: int = 1000, deg=(2, 5), net=(8, 64), grid
         surfs.append(surface(rng, p, q, n1, m1, nu, nv))
     targets = [twin_net(rng_t, s) for s in surfs]
     return surfs, targets
+
+def double_curved_net(n1: int = 12, amp: float = 0.25, rng: np.random.Generator | None = None,
+                      w_lo: float = 1.0, w_hi: float = 1.0) -> np.ndarray:
+    """A double-curved patch: z = amp sin(pi x) cos(pi y) sampled on an n1 x n1
+    grid of control points over [0,1]^2; weights U[w_lo, w_hi] (1 by default)."""
+    g = np.linspace(0.0, 1.0, n1, dtype=np.float64)
+    X, Y = np.meshgrid(g, g, indexing="ij")
+    net = np.zeros((n1, n1, 4), np.float32)
+    net[..., 0], net[..., 1] = X, Y
+    net[..., 2] = amp * np.sin(np.pi * X) * np.cos(np.pi * Y)
+    net[..., 3] = 1.0 if rng is None else rng.uniform(w_lo, w_hi, size=(n1, n1))
+    return net
+
+
+def offset_batch(seed: int = 0, batch: int = 4096, n1: int = 12, grid: int = 20):
+    """Bicubic double-curved patches (random amplitude and weights U[0.8, 1.2],
+    uniform knots) sampled on grid x grid points: the shape of the paper's
+    offsetting test surfaces."""
+    rng = np.random.default_rng(seed)
+    U = clamped_uniform_knots(n1, 3)
+    out = []
+    for _ in range(batch):
+        net = double_curved_net(n1, float(rng.uniform(0.1, 0.3)), rng, 0.8, 1.2)
+        out.append(Surface(3, 3, U, U, net, uniform_params(grid), uniform_params(grid)))
+    return out
