@@ -21,8 +21,8 @@
 // later lanes' overflow entries in lane order.  It then writes the Cartesian
 // gradient (and runs Adam, in a fit step), so results are deterministic.
 //
-// Parameters and dL/dS (or the MSE target) stream through a two-stage cp.async
-// ring per lane, kCurveRound samples a stage.
+// Parameters and dL/dS (or the MSE target) stream through a cp.async ring per
+// lane, kCurveStages rounds of kCurveRound samples deep.
 #pragma once
 #include "nurbs_tile.cuh"
 
@@ -30,6 +30,7 @@ namespace nurbs {
 
 constexpr int kCurveWarps = 4;        // curves in flight per CTA
 constexpr int kCurveRound = 4;        // samples per lane per staged round
+constexpr int kCurveStages = 2;       // rounds in flight per lane (power of two)
 constexpr int kCurveCtrlCap = 256;    // control points per curve on this path (larger: tile kernels)
 
 // Per-warp shared layout (bytes) for degree P and control capacity mc:
@@ -39,17 +40,22 @@ constexpr int kCurveCtrlCap = 256;    // control points per curve on this path (
 //   lanes  512           int[4][32]: first span, last span, previous lane's last span, -
 //   Aov    512 (P+1)     [32][P+1] float4: each lane's overflow block of control points
 //   Kov    256 P         [32][2P] floats: each lane's overflow block of knots
-//   ring   4096          [2][32][4] float4: per lane one chunk of 4 parameters and three
+//   net    16 mc         the curve's control points (x, y, z, w)
+//   ring   2048 stages   [stages][32][4] float4: per lane one chunk of 4 parameters and three
 //                        chunks of 4 targets (x y z); lane L's chunk c sits at slot
 //                        c ^ ((L >> 1) & 3) so that the lanes' 128-bit reads of one
 //                        chunk hit 8 distinct bank groups per quarter warp
 __host__ __device__ constexpr int curve_kc(int mc, int P) { return (mc + P + 1 + 3) & ~3; }
 __host__ __device__ constexpr int curve_off_aov(int mc, int P) { return 8 * curve_kc(mc, P) + 16 * mc + 512; }
-__host__ __device__ constexpr int curve_off_ring(int mc, int P)
+__host__ __device__ constexpr int curve_off_net(int mc, int P)
 {
     return (curve_off_aov(mc, P) + 512 * (P + 1) + 256 * P + 15) & ~15;
 }
-__host__ __device__ constexpr int curve_warp_bytes(int mc, int P) { return curve_off_ring(mc, P) + 2 * 32 * 16 * 4; }
+__host__ __device__ constexpr int curve_off_ring(int mc, int P) { return curve_off_net(mc, P) + 16 * mc; }
+__host__ __device__ constexpr int curve_warp_bytes(int mc, int P)
+{
+    return curve_off_ring(mc, P) + kCurveStages * 32 * 16 * 4;
+}
 
 template <int P, bool GRAD, bool KNOTS, bool MSE, bool DER = false>
 __device__ __forceinline__ void curve_body(const KParams& kp, int t, unsigned char* wsm)
@@ -66,6 +72,7 @@ __device__ __forceinline__ void curve_body(const KParams& kp, int t, unsigned ch
     int* s_ln = reinterpret_cast<int*>(wsm + 8 * kc + 16 * mc);
     float4* s_Aov = reinterpret_cast<float4*>(wsm + curve_off_aov(mc, P));
     float* s_Kov = reinterpret_cast<float*>(wsm + curve_off_aov(mc, P) + 512 * PB);
+    float4* s_net = reinterpret_cast<float4*>(wsm + curve_off_net(mc, P));
     float* s_ring = reinterpret_cast<float*>(wsm + curve_off_ring(mc, P));
 
     const int item = kp.tiles[t].item;
@@ -77,6 +84,8 @@ __device__ __forceinline__ void curve_body(const KParams& kp, int t, unsigned ch
     const float* __restrict__ gt = GRAD ? kp.gin + 3 * it.pts : nullptr;
 
     for (int k = lane; k < nk; k += 32) cp_async4(s_kn + k, gU + k);
+    for (int i = lane; i < nc; i += 32)
+        cp_async16(reinterpret_cast<float*>(s_net + i), reinterpret_cast<const float*>(gP + i));
     cp_async_commit();
 
     // this lane's samples [b0, b1): a whole number of rounds each (the last lane may be short)
@@ -90,7 +99,7 @@ __device__ __forceinline__ void curve_body(const KParams& kp, int t, unsigned ch
     auto issue = [&](int k) {
         if (k < rounds) {
             const int bb = b0 + k * R;
-            float* dst = s_ring + ((k & 1) * 32 + lane) * 16;
+            float* dst = s_ring + ((k & (kCurveStages - 1)) * 32 + lane) * 16;
             if (al16 && bb + R <= b1) {
                 cp_async16(dst + 4 * (0 ^ swz), gu + bb);
                 if constexpr (GRAD) {
@@ -116,9 +125,9 @@ __device__ __forceinline__ void curve_body(const KParams& kp, int t, unsigned ch
         }
         cp_async_commit();
     };
-    issue(0);
-    issue(1);
-    cp_async_wait<2>();   // the knots
+#pragma unroll
+    for (int k = 0; k < kCurveStages; ++k) issue(k);
+    cp_async_wait<kCurveStages>();   // the knots and the control net
     __syncwarp();
 
     // device checks and the spans of this lane's first and last samples
@@ -162,7 +171,7 @@ __device__ __forceinline__ void curve_body(const KParams& kp, int t, unsigned ch
     auto advance = [&](int s) {
         if (cur < 0) {
 #pragma unroll
-            for (int r = 0; r < PB; ++r) Qw[r] = homog(__ldg(gP + s - P + r));
+            for (int r = 0; r < PB; ++r) Qw[r] = homog(s_net[s - P + r]);
             cur = s;
             return;
         }
@@ -180,7 +189,7 @@ __device__ __forceinline__ void curve_body(const KParams& kp, int t, unsigned ch
                 kacc[KW - 1] = 0.f;
             }
             ++cur;
-            if (cur > s - PB) Qw[P] = homog(__ldg(gP + cur));   // only the last P+1 matter
+            if (cur > s - PB) Qw[P] = homog(s_net[cur]);   // only the last P+1 matter
         }
     };
 
@@ -245,8 +254,8 @@ __device__ __forceinline__ void curve_body(const KParams& kp, int t, unsigned ch
     // this lane's chunk offsets in a ring stage (floats)
     const int o0 = 4 * (0 ^ swz), o1 = 4 * (1 ^ swz), o2 = 4 * (2 ^ swz), o3 = 4 * (3 ^ swz);
     for (int k = 0; k < rounds; ++k) {
-        cp_async_wait<1>();   // round k has landed (round k+1 may be in flight)
-        const float* rb = s_ring + ((k & 1) * 32 + lane) * 16;
+        cp_async_wait<kCurveStages - 1>();   // round k has landed (later ones may be in flight)
+        const float* rb = s_ring + ((k & (kCurveStages - 1)) * 32 + lane) * 16;
         const int bb = b0 + k * R;
         // target word w = 3j + c of the round sits in chunk 1 + w / 4
 #pragma unroll
@@ -265,7 +274,7 @@ __device__ __forceinline__ void curve_body(const KParams& kp, int t, unsigned ch
             }
         }
         __syncwarp();
-        issue(k + 2);   // the stage just read is refilled two rounds ahead
+        issue(k + kCurveStages);   // the stage just read is refilled for a later round
     }
     if constexpr (GRAD) {
         if (cur >= 0) {
@@ -308,7 +317,7 @@ __device__ __forceinline__ void curve_body(const KParams& kp, int t, unsigned ch
                 const int i = i0 + 32 * e;
                 a[e] = c[e] = mm[e] = vv[e] = f4zero();
                 if (i >= nc) continue;
-                c[e] = gP[i];
+                c[e] = s_net[i];
                 if (kp.fit) { mm[e] = kp.adam_m[it.ctrl + i]; vv[e] = kp.adam_v[it.ctrl + i]; }
                 bool first = true;
                 for (int l = first_lane(i); l < nact && s_ln[l] - P <= i; ++l) {
