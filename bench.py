@@ -256,12 +256,18 @@ def run_ours(args):
     e2e_value = replicas.job_rate(npts * args.steps, e_ms / 1e3, dev)
 
     extras = {}
+    want = set(args.extras.split(",")) if args.extras else set()
+    xs = max(5, args.steps // 2)
     if rank == 0 and not args.no_extra:
-        extras["curves_fit_step"] = bench_curves(dev, max(5, args.steps // 2), args.warmup, flush, peak)
-        extras["tangents_normals"] = bench_derivs(dev, max(5, args.steps // 2), args.warmup, flush, peak, plan,
-                                                  kn, ct, pr, npts, pk.descs)
-        extras["ragged_graph"] = bench_ragged(dev, max(5, args.steps // 2), args.warmup, flush, peak)
-        extras["offset_fit"] = bench_offset(dev, max(5, args.steps // 2), args.warmup, flush, peak)
+        if "curves" in want:
+            extras["curves_fit_step"] = bench_curves(dev, xs, args.warmup, flush, peak)
+        if "derivs" in want:
+            extras["tangents_normals"] = bench_derivs(dev, xs, args.warmup, flush, peak, plan, kn, ct, pr, npts,
+                                                      pk.descs)
+        if "ragged" in want:
+            extras["ragged_graph"] = bench_ragged(dev, xs, args.warmup, flush, peak)
+        if "offset" in want:
+            extras["offset_fit"] = bench_offset(dev, xs, args.warmup, flush, peak)
     if rank == 0 and args.serve:
         extras["serving"] = bench_serve(dev, n_requests=args.serve_requests)
 
@@ -526,7 +532,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--no-extra", action="store_true", help="skip the curve and ragged workloads")
+    ap.add_argument("--no-extra", action="store_true", help="skip the extra workloads")
+    ap.add_argument("--extras", default="curves,derivs,ragged,offset",
+                    help="comma-separated extra workloads: curves, derivs, ragged, offset")
     ap.add_argument("--tile", default="", help="fixed tile shape 'warps,rows' instead of the autotuner's")
     ap.add_argument("--serve", action="store_true", help="also run the serving sweep (Poisson arrivals)")
     ap.add_argument("--serve-requests", type=int, default=20000)
