@@ -32,6 +32,9 @@
  *   - gradients are with respect to the Cartesian control points and the weights
  *     (Psi = {P, U, V, W}, Sec. 3).
  */
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
@@ -157,6 +160,65 @@ void nurbs_oracle_basis_knot_jac(int span, double u, int p, const double* U, dou
 }
 
 /* ---------------------------------------------------------------------------
+ * Knot Jacobian with the Gaussian-smoothed degree-0 indicator of Sec. 3.2 (the
+ * paper's own form of the knot derivative, bandwidth sigma > 0).  The forward
+ * stays exact; the degree-0 functions get the derivative of their smoothed
+ * form  N^0_j ~ Phi((u - U_j)/sigma) - Phi((u - U_{j+1})/sigma):
+ *   dN^0_j/dU_j = -G(u - U_j),   dN^0_j/dU_{j+1} = +G(u - U_{j+1}),
+ *   G(x) = exp(-x^2 / (2 sigma^2)) / (sigma sqrt(2 pi)),
+ * and both these and the recursion coefficients' derivatives are pushed
+ * through the full triangle of Eq. 4 (every function N^d_i with i in
+ * [span-p, span+p-d], zero-valued ones included), one knot at a time in
+ * forward mode.  Knots U[span-p .. span+p+1] (2p+2 of them);
+ * J[r*(2p+2) + k] = dN_{span-p+r}(u) / dU[span-p+k].  0/0 in a coefficient := 0.
+ * ------------------------------------------------------------------------- */
+static double gauss(double x, double sigma)
+{
+    return exp(-0.5 * (x / sigma) * (x / sigma)) / (sigma * sqrt(2.0 * M_PI));
+}
+
+void nurbs_oracle_basis_knot_jac_sigma(int span, double u, int p, const double* U, double sigma, double* N,
+                                       double* J)
+{
+    int K = 2 * p + 2, lo = span - p;
+    for (int k = 0; k < K; ++k) {
+        int kk = lo + k;                      /* the knot whose derivative this pass carries */
+        double val[2 * OR_MAXDEG + 1], dot[2 * OR_MAXDEG + 1];
+        for (int j = lo; j <= span + p; ++j) {
+            val[j - lo] = (j == span) ? 1.0 : 0.0;
+            double d = 0.0;
+            if (sigma > 0.0) {
+                if (j == kk) d -= gauss(u - U[j], sigma);
+                if (j + 1 == kk) d += gauss(u - U[j + 1], sigma);
+            }
+            dot[j - lo] = d;
+        }
+        for (int d = 1; d <= p; ++d) {
+            for (int i = lo; i <= span + p - d; ++i) {
+                double an = u - U[i], ad = U[i + d] - U[i];
+                double bn = U[i + d + 1] - u, bd = U[i + d + 1] - U[i + 1];
+                double dan = (i == kk) ? -1.0 : 0.0;
+                double dad = ((i + d == kk) ? 1.0 : 0.0) - ((i == kk) ? 1.0 : 0.0);
+                double dbn = (i + d + 1 == kk) ? 1.0 : 0.0;
+                double dbd = ((i + d + 1 == kk) ? 1.0 : 0.0) - ((i + 1 == kk) ? 1.0 : 0.0);
+                double al = 0.0, dal = 0.0, be = 0.0, dbe = 0.0;
+                if (ad != 0.0) { al = an / ad; dal = (dan * ad - an * dad) / (ad * ad); }
+                if (bd != 0.0) { be = bn / bd; dbe = (dbn * bd - bn * dbd) / (bd * bd); }
+                int t = i - lo;
+                double v = al * val[t] + be * val[t + 1];
+                double dv = dal * val[t] + al * dot[t] + dbe * val[t + 1] + be * dot[t + 1];
+                val[t] = v;      /* level d overwrites level d-1 in increasing i */
+                dot[t] = dv;
+            }
+        }
+        for (int r = 0; r <= p; ++r) {
+            if (k == 0) N[r] = val[r];
+            J[r * K + k] = dot[r];
+        }
+    }
+}
+
+/* ---------------------------------------------------------------------------
  * Surface forward (Eq. 3 evaluated as in Sec. 3.1: span, nonzero basis,
  * homogeneous weighted sum, perspective divide).
  * ------------------------------------------------------------------------- */
@@ -203,22 +265,37 @@ void nurbs_oracle_surface_eval(int p, int q, int n1, int m1, const double* U, co
  *               the knot derivative of Sec. 3.2), likewise dL/dV_k.
  * Outputs are overwritten.  Sum order: a, then b.
  * ------------------------------------------------------------------------- */
-void nurbs_oracle_surface_vjp(int p, int q, int n1, int m1, const double* U, const double* V,
-                              const double* ctrl, int nu, const double* u, int nv, const double* v,
-                              const double* g, double* dctrl, double* dU, double* dV)
+/* Knot Jacobian of one sample: the sigma -> 0 reading over the 2p knots
+ * [span-p+1, span+p] (sigma == 0), or the smoothed-indicator form over the 2p+2
+ * knots [span-p, span+p+1].  Returns the width; *base = first knot index. */
+static int knot_jacobian(int span, double u, int p, const double* U, double sigma, double* N, double* J, int* base)
+{
+    if (sigma > 0.0) {
+        nurbs_oracle_basis_knot_jac_sigma(span, u, p, U, sigma, N, J);
+        *base = span - p;
+        return 2 * p + 2;
+    }
+    nurbs_oracle_basis_knot_jac(span, u, p, U, N, J);
+    *base = span - p + 1;
+    return 2 * p;
+}
+
+void nurbs_oracle_surface_vjp_sigma(int p, int q, int n1, int m1, const double* U, const double* V,
+                                    const double* ctrl, int nu, const double* u, int nv, const double* v,
+                                    const double* g, double* dctrl, double* dU, double* dV, double sigma)
 {
     int nU = n1 + p + 1, nV = m1 + q + 1;
     if (dctrl) memset(dctrl, 0, sizeof(double) * 4 * (size_t)n1 * m1);
     if (dU) memset(dU, 0, sizeof(double) * nU);
     if (dV) memset(dV, 0, sizeof(double) * nV);
     double Nu[OR_MAXDEG + 1], Nv[OR_MAXDEG + 1];
-    double dNu[(OR_MAXDEG + 1) * 2 * OR_MAXDEG], dNv[(OR_MAXDEG + 1) * 2 * OR_MAXDEG];
+    double dNu[(OR_MAXDEG + 1) * (2 * OR_MAXDEG + 2)], dNv[(OR_MAXDEG + 1) * (2 * OR_MAXDEG + 2)];
     for (int a = 0; a < nu; ++a) {
         int su = nurbs_oracle_find_span(n1 - 1, p, u[a], U);
-        nurbs_oracle_basis_knot_jac(su, u[a], p, U, Nu, dNu);
+        int bu = 0, ku = knot_jacobian(su, u[a], p, U, sigma, Nu, dNu, &bu);
         for (int b = 0; b < nv; ++b) {
             int sv = nurbs_oracle_find_span(m1 - 1, q, v[b], V);
-            nurbs_oracle_basis_knot_jac(sv, v[b], q, V, Nv, dNv);
+            int bv = 0, kv = knot_jacobian(sv, v[b], q, V, sigma, Nv, dNv, &bv);
             /* NR (3-vector) and W of Eq. 6 */
             double NR[3] = {0, 0, 0}, W = 0;
             for (int r = 0; r <= p; ++r)
@@ -260,8 +337,8 @@ void nurbs_oracle_surface_vjp(int p, int q, int n1, int m1, const double* U, con
                     double coef = 0;
                     for (int c3 = 0; c3 < 3; ++c3)
                         coef += (Qi[c3] / W - NR[c3] * Qw / (W * W)) * ga[c3];
-                    for (int k = 0; k < 2 * p; ++k)
-                        dU[su - p + 1 + k] += coef * dNu[r * 2 * p + k];
+                    for (int k = 0; k < ku; ++k)
+                        dU[bu + k] += coef * dNu[r * ku + k];
                 }
             }
             if (dV) {
@@ -277,8 +354,8 @@ void nurbs_oracle_surface_vjp(int p, int q, int n1, int m1, const double* U, con
                     double coef = 0;
                     for (int c3 = 0; c3 < 3; ++c3)
                         coef += (Qi[c3] / W - NR[c3] * Qw / (W * W)) * ga[c3];
-                    for (int k = 0; k < 2 * q; ++k)
-                        dV[sv - q + 1 + k] += coef * dNv[h * 2 * q + k];
+                    for (int k = 0; k < kv; ++k)
+                        dV[bv + k] += coef * dNv[h * kv + k];
                 }
             }
         }
@@ -286,6 +363,13 @@ void nurbs_oracle_surface_vjp(int p, int q, int n1, int m1, const double* U, con
     /* end knots carry no gradient (fixed domain) */
     if (dU) for (int k = 0; k < nU; ++k) if (k < p + 1 || k > n1 - 1) dU[k] = 0.0;
     if (dV) for (int k = 0; k < nV; ++k) if (k < q + 1 || k > m1 - 1) dV[k] = 0.0;
+}
+
+void nurbs_oracle_surface_vjp(int p, int q, int n1, int m1, const double* U, const double* V,
+                              const double* ctrl, int nu, const double* u, int nv, const double* v,
+                              const double* g, double* dctrl, double* dU, double* dV)
+{
+    nurbs_oracle_surface_vjp_sigma(p, q, n1, m1, U, V, ctrl, nu, u, nv, v, g, dctrl, dU, dV, 0.0);
 }
 
 /* ---------------------------------------------------------------------------
@@ -313,16 +397,17 @@ void nurbs_oracle_curve_eval(int p, int n1, const double* U, const double* ctrl,
     }
 }
 
-void nurbs_oracle_curve_vjp(int p, int n1, const double* U, const double* ctrl,
-                            int nu, const double* u, const double* g, double* dctrl, double* dU)
+void nurbs_oracle_curve_vjp_sigma(int p, int n1, const double* U, const double* ctrl,
+                                  int nu, const double* u, const double* g, double* dctrl, double* dU,
+                                  double sigma)
 {
     int nU = n1 + p + 1;
     if (dctrl) memset(dctrl, 0, sizeof(double) * 4 * (size_t)n1);
     if (dU) memset(dU, 0, sizeof(double) * nU);
-    double N[OR_MAXDEG + 1], dN[(OR_MAXDEG + 1) * 2 * OR_MAXDEG];
+    double N[OR_MAXDEG + 1], dN[(OR_MAXDEG + 1) * (2 * OR_MAXDEG + 2)];
     for (int a = 0; a < nu; ++a) {
         int s = nurbs_oracle_find_span(n1 - 1, p, u[a], U);
-        nurbs_oracle_basis_knot_jac(s, u[a], p, U, N, dN);
+        int base = 0, kw = knot_jacobian(s, u[a], p, U, sigma, N, dN, &base);
         double NR[3] = {0, 0, 0}, W = 0;
         for (int r = 0; r <= p; ++r) {
             const double* c = ctrl + 4 * (s - p + r);
@@ -346,12 +431,18 @@ void nurbs_oracle_curve_vjp(int p, int n1, const double* U, const double* ctrl,
                 double coef = 0;
                 for (int c3 = 0; c3 < 3; ++c3)
                     coef += (c[3] * c[c3] / W - NR[c3] * c[3] / (W * W)) * ga[c3];
-                for (int k = 0; k < 2 * p; ++k)
-                    dU[s - p + 1 + k] += coef * dN[r * 2 * p + k];
+                for (int k = 0; k < kw; ++k)
+                    dU[base + k] += coef * dN[r * kw + k];
             }
         }
     }
     if (dU) for (int k = 0; k < nU; ++k) if (k < p + 1 || k > n1 - 1) dU[k] = 0.0;
+}
+
+void nurbs_oracle_curve_vjp(int p, int n1, const double* U, const double* ctrl,
+                            int nu, const double* u, const double* g, double* dctrl, double* dU)
+{
+    nurbs_oracle_curve_vjp_sigma(p, n1, U, ctrl, nu, u, g, dctrl, dU, 0.0);
 }
 
 /* ---------------------------------------------------------------------------

@@ -10,6 +10,7 @@ inputs the GPU path sees) and calls the C routine of the same role:
 * ``find_span``, ``basis_funs``        -- span search and nonzero basis (Sec. 3.1 steps 1-2)
 * ``basis_cox_de_boor``               -- brute-force recursion, Eq. 4 / Eq. 5
 * ``basis_knot_jac``                  -- knot Jacobian of the nonzero basis (Sec. 3.2)
+* ``basis_knot_jac_sigma``            -- the same with the Gaussian-smoothed indicator term
 * ``surface_eval`` / ``curve_eval``   -- Eq. 3 (and its one-direction form)
 * ``surface_vjp`` / ``curve_vjp``     -- Eq. 7, Eq. 8, Eq. 9 + knot derivative
 * ``basis_ders``                      -- u-derivative of the nonzero basis (of Eq. 4)
@@ -59,6 +60,9 @@ def lib():
             L.nurbs_oracle_basis_knot_jac.argtypes = [i, d, i, _D, _D, _D]
             L.nurbs_oracle_surface_eval.argtypes = [i, i, i, i, _D, _D, _D, i, _D, i, _D, _D]
             L.nurbs_oracle_surface_vjp.argtypes = [i, i, i, i, _D, _D, _D, i, _D, i, _D, _D, _D, _D, _D]
+            L.nurbs_oracle_surface_vjp_sigma.argtypes = [i, i, i, i, _D, _D, _D, i, _D, i, _D, _D, _D, _D, _D, d]
+            L.nurbs_oracle_curve_vjp_sigma.argtypes = [i, i, _D, _D, i, _D, _D, _D, _D, d]
+            L.nurbs_oracle_basis_knot_jac_sigma.argtypes = [i, d, i, _D, d, _D, _D]
             L.nurbs_oracle_curve_eval.argtypes = [i, i, _D, _D, i, _D, _D]
             L.nurbs_oracle_curve_vjp.argtypes = [i, i, _D, _D, i, _D, _D, _D, _D]
             L.nurbs_oracle_basis_ders.argtypes = [i, d, i, _D, _D]
@@ -106,6 +110,16 @@ def basis_knot_jac(span: int, u: float, p: int, U):
     return N, dN.reshape(p + 1, max(2 * p, 1))[:, : 2 * p]
 
 
+def basis_knot_jac_sigma(span: int, u: float, p: int, U, sigma: float):
+    """(N[p+1], J[p+1, 2p+2]) with J[r, k] = dN_{span-p+r}/dU[span-p+k] including
+    the Gaussian-smoothed indicator term of bandwidth sigma (Sec. 3.2)."""
+    U = _f64(U)
+    N = np.zeros(p + 1)
+    J = np.zeros((p + 1) * (2 * p + 2))
+    lib().nurbs_oracle_basis_knot_jac_sigma(span, float(u), p, _p(U), float(sigma), _p(N), _p(J))
+    return N, J.reshape(p + 1, 2 * p + 2)
+
+
 # ------------------------------------------------------------------- surface
 def surface_eval(p, q, U, V, ctrl, u, v) -> np.ndarray:
     """ctrl: [n1, m1, 4] (x, y, z, w).  Returns S[nu, nv, 3] in float64."""
@@ -118,8 +132,9 @@ def surface_eval(p, q, U, V, ctrl, u, v) -> np.ndarray:
     return out
 
 
-def surface_vjp(p, q, U, V, ctrl, u, v, g, want_ctrl=True, want_knots=True):
-    """Returns (dctrl[n1, m1, 4], dU, dV); entries not requested are None."""
+def surface_vjp(p, q, U, V, ctrl, u, v, g, want_ctrl=True, want_knots=True, knot_sigma=0.0):
+    """Returns (dctrl[n1, m1, 4], dU, dV); entries not requested are None.
+    knot_sigma > 0 takes the knot derivative in its Gaussian-smoothed form."""
     ctrl = _f64(ctrl)
     n1, m1 = ctrl.shape[0], ctrl.shape[1]
     U, V, u, v, g = _f64(U), _f64(V), _f64(u), _f64(v), _f64(g)
@@ -127,8 +142,8 @@ def surface_vjp(p, q, U, V, ctrl, u, v, g, want_ctrl=True, want_knots=True):
     dctrl = np.zeros((n1, m1, 4)) if want_ctrl else None
     dU = np.zeros(len(U)) if want_knots else None
     dV = np.zeros(len(V)) if want_knots else None
-    lib().nurbs_oracle_surface_vjp(p, q, n1, m1, _p(U), _p(V), _p(ctrl), len(u), _p(u), len(v), _p(v),
-                                   _p(g), _p(dctrl), _p(dU), _p(dV))
+    lib().nurbs_oracle_surface_vjp_sigma(p, q, n1, m1, _p(U), _p(V), _p(ctrl), len(u), _p(u), len(v), _p(v),
+                                         _p(g), _p(dctrl), _p(dU), _p(dV), float(knot_sigma))
     return dctrl, dU, dV
 
 
@@ -143,13 +158,14 @@ def curve_eval(p, U, ctrl, u) -> np.ndarray:
     return out
 
 
-def curve_vjp(p, U, ctrl, u, g, want_ctrl=True, want_knots=True):
+def curve_vjp(p, U, ctrl, u, g, want_ctrl=True, want_knots=True, knot_sigma=0.0):
     ctrl = _f64(ctrl)
     n1 = ctrl.shape[0]
     U, u, g = _f64(U), _f64(u), _f64(g)
     dctrl = np.zeros((n1, 4)) if want_ctrl else None
     dU = np.zeros(len(U)) if want_knots else None
-    lib().nurbs_oracle_curve_vjp(p, n1, _p(U), _p(ctrl), len(u), _p(u), _p(g), _p(dctrl), _p(dU))
+    lib().nurbs_oracle_curve_vjp_sigma(p, n1, _p(U), _p(ctrl), len(u), _p(u), _p(g), _p(dctrl), _p(dU),
+                                       float(knot_sigma))
     return dctrl, dU
 
 
