@@ -129,6 +129,23 @@ nurbs_status nurbs_plan_bind(nurbs_plan* plan, void* d_workspace, size_t bytes, 
 void nurbs_plan_destroy(nurbs_plan* plan);
 
 /*
+ * nurbs_plan_set_knot_sigma -- choose the knot derivative of later backward,
+ * MSE and fit-step calls on this plan (host only).
+ *   sigma == 0 (the default): the exact almost-everywhere derivative of Eq. 4,
+ *     i.e. the degree-0 indicators' knot derivative taken as 0 (the sigma -> 0
+ *     limit of Sec. 3.2).
+ *   sigma > 0: the paper's Gaussian-smoothed indicator.  The degree-0 function
+ *     N^0_j gets the knot derivative -G(u - U_j) at U_j and +G(u - U_{j+1}) at
+ *     U_{j+1}, with G(x) = exp(-x^2 / 2 sigma^2) / (sigma sqrt(2 pi)).  These
+ *     terms are pushed through the Cox-de Boor triangle, and each sample adds
+ *     them for the 2p knots it already touches.  The knots one step further out
+ *     lie at least p spans away and are left out.
+ * The end knots still get 0.  Errors: NURBS_ERR_ARG for a negative or
+ * non-finite sigma.
+ */
+nurbs_status nurbs_plan_set_knot_sigma(nurbs_plan* plan, float sigma);
+
+/*
  * nurbs_plan_get_error -- synchronise `stream`, read and clear the device error
  * word written by the device-side checks of earlier calls.  *flags receives the
  * raw bit set (bit k set <=> status k was raised); returns the lowest raised

@@ -103,6 +103,7 @@ SIGNATURES = {
     "nurbs_plan_points": (_i64, [_vp]),
     "nurbs_plan_tiles": (_i32, [_vp]),
     "nurbs_plan_ctas": (_i32, [_vp]),
+    "nurbs_plan_set_knot_sigma": (_i32, [_vp, _f]),
     "nurbs_plan_bind": (_i32, [_vp, _vp, _sz, _vp]),
     "nurbs_plan_destroy": (None, [_vp]),
     "nurbs_plan_get_error": (_i32, [_vp, _vp, ctypes.POINTER(ctypes.c_uint32)]),

@@ -170,6 +170,11 @@ class Plan:
         _lib.check(fn(self.handle, _ptr(knots), _ptr(ctrl), _ptr(params), _ptr(pts), _stream(stream)), fn.__name__)
         return pts
 
+    def set_knot_sigma(self, sigma: float):
+        """Knot derivative of later gradient calls: 0 = almost-everywhere form,
+        > 0 = the Gaussian-smoothed indicator of bandwidth sigma."""
+        _lib.check(self.lib.nurbs_plan_set_knot_sigma(self.handle, ctypes.c_float(sigma)), "nurbs_plan_set_knot_sigma")
+
     def eval_derivs(self, knots, ctrl, params, pts=None, du=None, dv=None, normals=None, stream=None):
         """Points with tangents and unit normals (surfaces: du, dv, normals; curves:
         the tangent goes to ``du``).  Outputs that are None are not written."""

@@ -58,6 +58,7 @@ struct nurbs_plan {
     int smem_bytes;           // gradient kernels
     int smem_eval;            // forward kernels (no shared adjoint)
     int c_mc, c_wbytes, c_smem;   // curve kernels: control capacity, bytes per warp, per CTA
+    float knot_sigma;             // smoothed-indicator knot derivative bandwidth (0: off)
     // workspace layout (bytes)
     size_t items_off, tiles_off, counts_off, part_off, ws_bytes;
     // binding
@@ -302,6 +303,13 @@ nurbs_status nurbs_plan_create(int32_t kind, const nurbs_desc* h_desc, int32_t c
 }
 
 size_t nurbs_plan_workspace_size(const nurbs_plan* plan) { return plan ? plan->ws_bytes : 0; }
+
+nurbs_status nurbs_plan_set_knot_sigma(nurbs_plan* plan, float sigma)
+{
+    if (plan == nullptr || !(sigma >= 0.f) || !std::isfinite(sigma)) return NURBS_ERR_ARG;
+    plan->knot_sigma = sigma;
+    return NURBS_OK;
+}
 int64_t nurbs_plan_points(const nurbs_plan* plan) { return plan ? plan->points : 0; }
 int32_t nurbs_plan_tiles(const nurbs_plan* plan) { return plan ? (int32_t)plan->tiles.size() : 0; }
 
@@ -414,6 +422,7 @@ void fill_tables(KParams& kp, const nurbs_plan* pl, unsigned char* ws)
     kp.acc_cap = pl->acc_cap;
     kp.c_mc = pl->c_mc;
     kp.c_wbytes = pl->c_wbytes;
+    kp.knot_sigma = pl->knot_sigma;
 }
 
 // Launch variant v (0 forward, 1/2 backward from dL/dS without/with knots, 3/4 the

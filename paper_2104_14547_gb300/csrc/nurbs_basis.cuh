@@ -150,4 +150,51 @@ __device__ __forceinline__ void basis_knot_vjp(int s, float u, const float* U,
     }
 }
 
+// The Gaussian-smoothed indicator term of the knot derivative (Sec. 3.2, the
+// paper's form with bandwidth sigma > 0), added to dk of basis_knot_vjp.
+//
+// The degree-0 functions' smoothed knot derivatives, -G(u - U_j) at U_j and
+// +G(u - U_{j+1}) at U_{j+1} with G(x) = exp(-x^2 / 2 sigma^2) / (sigma sqrt(2 pi)),
+// reach dL/dU_k through the adjoints of every degree-0 function N^0_j,
+// j in [s-P, s+P].  Those adjoints are the cotangent nb pushed back through the
+// full triangle of Eq. 4 (zero-valued functions included; a coefficient with a
+// zero denominator is 0):
+//   dk[k - (s-P+1)] += G(u - U_k) (adj N^0_{k-1} - adj N^0_k),  k in [s-P+1, s+P].
+// The two knots just outside the window, U_{s-P} and U_{s+P+1}, lie at least P
+// spans from u; their terms are left out.
+template <int P>
+__device__ __forceinline__ void knot_sigma_terms(int s, float u, const float* U, const float (&nb)[P + 1],
+                                                 float sigma, float (&dk)[2 * P + 1])
+{
+    if constexpr (P > 0) {
+        float a[2 * P + 1];   // a[t]: adjoint of N^d_{s-P+t} at the current level d
+#pragma unroll
+        for (int t = 0; t <= 2 * P; ++t) a[t] = t <= P ? nb[t] : 0.f;
+#pragma unroll
+        for (int d = P; d >= 1; --d) {
+            float b[2 * P + 1];
+#pragma unroll
+            for (int t = 0; t <= 2 * P; ++t) b[t] = 0.f;
+#pragma unroll
+            for (int t = 0; t <= 2 * P - d; ++t) {
+                const int i = s - P + t;
+                const float ad = U[i + d] - U[i], bd = U[i + d + 1] - U[i + 1];
+                const float al = ad > 0.f ? (u - U[i]) * frcp(ad) : 0.f;
+                const float be = bd > 0.f ? (U[i + d + 1] - u) * frcp(bd) : 0.f;
+                b[t] = fmaf(al, a[t], b[t]);
+                b[t + 1] = fmaf(be, a[t], b[t + 1]);
+            }
+#pragma unroll
+            for (int t = 0; t <= 2 * P; ++t) a[t] = b[t];
+        }
+        const float is = frcp(sigma);
+        const float gn = 0.3989422804014327f * is;   // 1 / (sigma sqrt(2 pi))
+#pragma unroll
+        for (int k = 0; k < 2 * P; ++k) {
+            const float x = (u - U[s - P + 1 + k]) * is;
+            dk[k] = fmaf(gn * expf(-0.5f * x * x), a[k] - a[k + 1], dk[k]);
+        }
+    }
+}
+
 }  // namespace nurbs

@@ -245,6 +245,7 @@ __device__ __forceinline__ void curve_body(const KParams& kp, int t, unsigned ch
                 for (int r = 0; r < PB; ++r) beta[r] = dot4(Qw[r], lam);
                 float dk[2 * P + 1];
                 basis_knot_vjp<P>(s, u, s_kn, beta, dk);
+                if (kp.knot_sigma > 0.f) knot_sigma_terms<P>(s, u, s_kn, beta, kp.knot_sigma, dk);
 #pragma unroll
                 for (int q = 0; q < KW; ++q) kacc[q] += dk[q];
             }

@@ -77,6 +77,7 @@ struct KParams {
     float* d_dv;
     float* d_nrm;
     int c_mc, c_wbytes;      // curve kernels: control-point capacity, shared bytes per warp
+    float knot_sigma;        // > 0: knot derivative with the Gaussian-smoothed indicator term
 };
 
 __device__ __forceinline__ float4 f4zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
@@ -1043,7 +1044,9 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
                                 for (int k = 0; k < PB; ++k) bsum[k] += bw[k];
                             }
                             float dk[2 * P + 1];
-                            basis_knot_vjp<P>(s_su[r], fminf(fmaxf(s_u[r], ulo), uhi), s_knU, bsum, dk);
+                            const float ur = fminf(fmaxf(s_u[r], ulo), uhi);
+                            basis_knot_vjp<P>(s_su[r], ur, s_knU, bsum, dk);
+                            if (kp.knot_sigma > 0.f) knot_sigma_terms<P>(s_su[r], ur, s_knU, bsum, kp.knot_sigma, dk);
 #pragma unroll
                             for (int k = 0; k < 2 * P; ++k) s_duc[r * KU + k] = dk[k];
                         }
@@ -1057,7 +1060,9 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
                             for (int h = 0; h < QB; ++h) G[h] += s_dvc[(g * kp.C + c) * KV + h];
                         }
                         float dk[2 * Q + 1];
-                        basis_knot_vjp<Q>(s_sv[c], fminf(fmaxf(s_v[c], vlo), vhi), s_knV, G, dk);
+                        const float vc = fminf(fmaxf(s_v[c], vlo), vhi);
+                        basis_knot_vjp<Q>(s_sv[c], vc, s_knV, G, dk);
+                        if (kp.knot_sigma > 0.f) knot_sigma_terms<Q>(s_sv[c], vc, s_knV, G, kp.knot_sigma, dk);
 #pragma unroll
                         for (int k = 0; k < 2 * Q; ++k) s_dvc[c * KV + k] = dk[k];   // group 0's slot
                     }

@@ -91,3 +91,18 @@ def test_status_strings():
     lib = _lib.load()
     for k in range(10):
         assert lib.nurbs_status_string(k).decode()
+
+
+def test_knot_sigma_setter_validates():
+    s = synth.single_bicubic(0)
+    pk = batch.pack_surfaces([s])
+    st, h = _plan(_lib.KIND_SURFACE, pk.descs)
+    assert st == 0
+    lib = _lib.load()
+    assert lib.nurbs_plan_set_knot_sigma(h, 0.0) == 0
+    assert lib.nurbs_plan_set_knot_sigma(h, 1e-3) == 0
+    assert lib.nurbs_plan_set_knot_sigma(h, -1e-3) == 1
+    assert lib.nurbs_plan_set_knot_sigma(h, float("nan")) == 1
+    assert lib.nurbs_plan_set_knot_sigma(h, float("inf")) == 1
+    assert lib.nurbs_plan_set_knot_sigma(None, 1e-3) == 1
+    lib.nurbs_plan_destroy(h)
