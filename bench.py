@@ -268,8 +268,11 @@ def run_ours(args):
             extras["ragged_graph"] = bench_ragged(dev, xs, args.warmup, flush, peak)
         if "offset" in want:
             extras["offset_fit"] = bench_offset(dev, xs, args.warmup, flush, peak)
-    if rank == 0 and args.serve:
-        extras["serving"] = bench_serve(dev, n_requests=args.serve_requests)
+    if rank == 0 and not args.no_extra and ("serve" in want or args.serve):
+        if args.serve:       # the full sweep
+            extras["serving"] = bench_serve(dev, n_requests=args.serve_requests)
+        else:                # a short sweep (p50/p99 per rate) in the default run
+            extras["serving"] = bench_serve(dev, rates=(1000, 5000, 20000, 50000), n_requests=3000)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -533,10 +536,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-extra", action="store_true", help="skip the extra workloads")
-    ap.add_argument("--extras", default="curves,derivs,ragged,offset",
-                    help="comma-separated extra workloads: curves, derivs, ragged, offset")
+    ap.add_argument("--extras", default="curves,derivs,ragged,offset,serve",
+                    help="comma-separated extra workloads: curves, derivs, ragged, offset, serve (short sweep)")
     ap.add_argument("--tile", default="", help="fixed tile shape 'warps,rows' instead of the autotuner's")
-    ap.add_argument("--serve", action="store_true", help="also run the serving sweep (Poisson arrivals)")
+    ap.add_argument("--serve", action="store_true", help="run the full serving sweep (Poisson arrivals)")
     ap.add_argument("--serve-requests", type=int, default=20000)
     args = ap.parse_args()
     if args.warmup < 3:

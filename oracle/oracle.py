@@ -16,6 +16,7 @@ inputs the GPU path sees) and calls the C routine of the same role:
 * ``basis_ders``                      -- u-derivative of the nonzero basis (of Eq. 4)
 * ``surface_derivs`` / ``curve_derivs`` -- tangents S_u, S_v, unit normals (curve: C')
 * ``mse``, ``adam``                   -- the L2 (MSE) loss and the Adam step of Sec. 4
+* ``nearest``, ``chamfer``            -- Chamfer and Hausdorff distances of Sec. 4 (numpy)
 """
 from __future__ import annotations
 
@@ -209,3 +210,51 @@ def adam(theta, g, m, v, t: int, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
     theta, g, m, v = _f64(theta).copy(), _f64(g), _f64(m).copy(), _f64(v).copy()
     lib().nurbs_oracle_adam(theta.size, _p(theta), _p(g), _p(m), _p(v), int(t), lr, b1, b2, eps)
     return theta, m, v
+
+
+# ------------------------------------------------------- point-set distances
+def _d2_f32(A, B):
+    """Squared distances in float32, each as ((dx*dx + dy*dy) + dz*dz) with
+    every operation rounded separately: the precision the argmin is decided in."""
+    A32, B32 = np.asarray(A, np.float32), np.asarray(B, np.float32)
+    d = A32[:, None, :] - B32[None, :, :]
+    return (d[..., 0] * d[..., 0] + d[..., 1] * d[..., 1]) + d[..., 2] * d[..., 2]
+
+
+def nearest(A, B):
+    """For every point of A: index of its nearest point of B (the first one on
+    ties, decided on float32 squared distances) and the FP64 distance to it."""
+    A, B = np.asarray(A, np.float64).reshape(-1, 3), np.asarray(B, np.float64).reshape(-1, 3)
+    if len(A) == 0 or len(B) == 0:
+        return np.full(len(A), -1, np.int64), np.zeros(len(A))
+    nn = np.argmin(_d2_f32(A, B), axis=1)
+    return nn, np.linalg.norm(A - B[nn], axis=1)
+
+
+def chamfer(P, Q):
+    """The paper's point-set losses (Sec. 4): Chamfer distance
+    L_CD = sum_i min_j |P_i - Q_j| + sum_j min_i |P_i - Q_j| and Hausdorff distance
+    L_HD = max_i min_j |P_i - Q_j| + max_j min_i |P_i - Q_j|, with their gradients
+    with respect to P.  Returns (cd, hd, grad_cd[nP, 3], grad_hd[nP, 3], nn_p, nn_q).
+    A zero distance contributes no gradient; ties in argmax take the first index;
+    an empty set gives 0 and zero gradients."""
+    P, Q = np.asarray(P, np.float64).reshape(-1, 3), np.asarray(Q, np.float64).reshape(-1, 3)
+    gcd, ghd = np.zeros_like(P), np.zeros_like(P)
+    nn_p, d_p = nearest(P, Q)
+    nn_q, d_q = nearest(Q, P)
+    if len(P) == 0 or len(Q) == 0:
+        return 0.0, 0.0, gcd, ghd, nn_p, nn_q
+    cd = d_p.sum() + d_q.sum()
+    hd = d_p.max() + d_q.max()
+    for i in range(len(P)):
+        if d_p[i] > 0:
+            gcd[i] += (P[i] - Q[nn_p[i]]) / d_p[i]
+    for j in range(len(Q)):
+        if d_q[j] > 0:
+            gcd[nn_q[j]] += (P[nn_q[j]] - Q[j]) / d_q[j]
+    i_star, j_star = int(np.argmax(d_p)), int(np.argmax(d_q))
+    if d_p[i_star] > 0:
+        ghd[i_star] += (P[i_star] - Q[nn_p[i_star]]) / d_p[i_star]
+    if d_q[j_star] > 0:
+        ghd[nn_q[j_star]] += (P[nn_q[j_star]] - Q[j_star]) / d_q[j_star]
+    return float(cd), float(hd), gcd, ghd, nn_p, nn_q
