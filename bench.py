@@ -268,6 +268,8 @@ def run_ours(args):
             extras["ragged_graph"] = bench_ragged(dev, xs, args.warmup, flush, peak)
         if "offset" in want:
             extras["offset_fit"] = bench_offset(dev, xs, args.warmup, flush, peak)
+        if "chamfer" in want:
+            extras["chamfer"] = bench_chamfer(dev, xs, args.warmup, flush)
     if rank == 0 and not args.no_extra and ("serve" in want or args.serve):
         if args.serve:       # the full sweep
             extras["serving"] = bench_serve(dev, n_requests=args.serve_requests)
@@ -420,6 +422,35 @@ def bench_offset(dev, steps, warmup, flush, peak, count=4096):
                          "algorithmic_bytes": abytes}}
 
 
+def bench_chamfer(dev, steps, warmup, flush, count=256, grid=64):
+    """Chamfer + Hausdorff distances with gradients between the bench surfaces
+    evaluated on grid x grid samples and their target surfaces (count pairs of
+    grid^2 points each).  ALU-bound: every point meets every point of the other
+    set in each direction."""
+    import torch
+    from paper_2104_14547_gb300 import batch, losses, synth
+    surfs, targets = synth.bicubic_batch(0, count, WORKLOAD["net"], grid)
+    pk, tk = batch.pack_surfaces(surfs), batch.pack_surfaces(targets)
+    kn, ct, pr = batch.to_device(pk, dev)
+    _, tct, _ = batch.to_device(tk, dev)
+    S = torch.empty((pk.npts, 3), device=dev)
+    T = torch.empty((pk.npts, 3), device=dev)
+    batch.Plan.for_packed(pk, device=dev).eval(kn, ct, pr, S)
+    batch.Plan.for_packed(tk, device=dev).eval(kn, tct, pr, T)
+    sizes = [grid * grid] * count
+    stream = torch.cuda.current_stream(dev)
+    ms = _time_steps(lambda: losses.chamfer(S, sizes, T, sizes), steps, warmup, flush, stream)
+    evals = 2 * count * (grid * grid) ** 2          # point-to-point distances, both directions
+    ops = 9 * evals                                  # 3 sub, 3 mul, 2 add, 1 compare per distance
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak_ops = sms * 128 * 2.07e9                    # FP32 lanes x max SM clock
+    return {"workload": f"Chamfer + Hausdorff with gradients, {count} pairs of {grid}x{grid}-point surface samples",
+            "value": evals / (ms / 1e3), "unit": "point pairs/s", "ms_per_step": ms,
+            "roofline": {"bound": "alu", "achieved": ops / (ms / 1e3) / 1e12, "peak": peak_ops / 1e12,
+                         "unit": "TFLOP/s (FP32 non-FMA ops)", "frac": ops / (ms / 1e3) / peak_ops,
+                         "peak_source": "152 SMs x 128 FP32 lanes x 2070 MHz"}}
+
+
 def bench_ragged(dev, steps, warmup, flush, peak, count=1000):
     """1000 surfaces, degrees 2..5, nets 8..64 and grids 32..256 per direction:
     fwd + MSE + bwd through the CUDA-graph engine, against one launch per surface."""
@@ -536,8 +567,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-extra", action="store_true", help="skip the extra workloads")
-    ap.add_argument("--extras", default="curves,derivs,ragged,offset,serve",
-                    help="comma-separated extra workloads: curves, derivs, ragged, offset, serve (short sweep)")
+    ap.add_argument("--extras", default="curves,derivs,ragged,offset,chamfer,serve",
+                    help="comma-separated extra workloads: curves, derivs, ragged, offset, chamfer, serve (short sweep)")
     ap.add_argument("--tile", default="", help="fixed tile shape 'warps,rows' instead of the autotuner's")
     ap.add_argument("--serve", action="store_true", help="run the full serving sweep (Poisson arrivals)")
     ap.add_argument("--serve-requests", type=int, default=20000)

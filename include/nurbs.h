@@ -266,6 +266,35 @@ nurbs_status nurbs_mse_fwd_bwd_noalloc(const nurbs_plan* plan, const float* knot
                                        float* grad_ctrl, float* grad_knots, float* loss_items,
                                        float grad_scale, nurbs_stream_t stream);
 
+
+/*
+ * nurbs_chamfer -- the paper's point-set losses (Sec. 4) over `count` pairs of
+ * point sets, with their gradients with respect to the first set.  Pair k has
+ * points P[p_off[k] .. p_off[k+1]) and Q[q_off[k] .. q_off[k+1]):
+ *   L_CD = sum_i min_j |P_i - Q_j| + sum_j min_i |P_i - Q_j|      (Chamfer)
+ *   L_HD = max_i min_j |P_i - Q_j| + max_j min_i |P_i - Q_j|      (Hausdorff)
+ * All arrays are device arrays.
+ *   P, Q                points, [n][3] floats.
+ *   p_off, q_off        int64 offsets in points, count+1 of them, non-decreasing.
+ *   max_p, max_q        host bounds on the largest set of each side (grid size);
+ *                       points beyond them are not processed.
+ *   nn_p, dist_p        outputs, one per point of P: pair-local index of the
+ *                       nearest Q point (-1 if the pair's Q is empty) and the
+ *                       distance to it.  nn_q, dist_q: the same for Q.
+ *   cd, hd              optional outputs, one per pair.
+ *   grad_cd, grad_hd    optional outputs, [n][3] like P: gradients of L_CD and L_HD.
+ * Nearest points are decided on float32 squared distances, each rounded as
+ * ((dx dx + dy dy) + dz dz); ties go to the first index.  A zero distance
+ * contributes no gradient.  A pair with an empty side gives 0 and zero
+ * gradients.  Asynchronous on `stream`; no allocation; deterministic.
+ * Errors: NURBS_ERR_ARG (negative sizes, a missing required array),
+ * NURBS_ERR_SIZE (count > 65535), NURBS_ERR_CUDA.
+ */
+nurbs_status nurbs_chamfer(int32_t count, const int64_t* p_off, const int64_t* q_off, int32_t max_p, int32_t max_q,
+                           const float* P, const float* Q, int32_t* nn_p, float* dist_p, int32_t* nn_q,
+                           float* dist_q, float* cd, float* hd, float* grad_cd, float* grad_hd,
+                           nurbs_stream_t stream);
+
 /* Human-readable name of a status code (static string). */
 const char* nurbs_status_string(nurbs_status status);
 
