@@ -1,9 +1,10 @@
 // The libnurbs tile kernels.
 //
 // Work decomposition.  A surface item is cut into tiles of consecutive sample
-// rows (u) and up to 32*warps sample columns (v).  A curve item is mapped onto
-// the v direction (degree-0 u direction with a single row), so one code path
-// serves both.  The warps of a tile form `nwr` units (row groups) of `nwc`
+// rows (u) and up to 32*warps sample columns (v).  A curve too long for the curve
+// kernels (nurbs_curve.cuh) is mapped onto the v direction (degree-0 u direction
+// with a single row), so one code path serves both.  The warps of a tile form
+// `nwr` units (row groups) of `nwc`
 // column warps; lane b of a warp keeps its column's span and v-basis in
 // registers and walks the rows of its unit in order.  Because the samples are
 // non-decreasing, the u-span never decreases along that walk, so the lane holds
@@ -15,15 +16,17 @@
 // homogeneous adjoint lambda = (g / W, -S.g / W):
 //   tau[r](b)   = sum_a Nu_r(a) lambda_ab         (same sliding window, registers)
 //   A[i][j]     = sum_b Nv_{j-s_v(b)+Q}(b) tau[i](b)
-//                 (rows leaving the window are staged in shared memory, KB at a
+//                 (rows leaving the window are staged in shared memory, kBatch at a
 //                  time, and contracted over all tile columns by the whole unit in
 //                  a fixed order: a segmented reduction with no atomics)
 //   beta_r(a)   = sum_b Qw[r](b) . lambda_ab       (warp shuffle reduction)
 //   Gamma_h(b)  = sum_i tau[i](b) . Pw[i][s_v(b)-Q+h]
 // dL/dU and dL/dV follow from beta and Gamma by the reverse-mode knot derivative
-// of the basis.  Unit partials go to the workspace; the last CTA to finish a
-// tile of an item adds them in unit order, so every result is independent of
-// scheduling (bit-identical run to run, alone or in any batch).
+// of the basis.  An item that is a single tile keeps its adjoint in shared
+// memory and the CTA finishes it alone; otherwise unit partials go to the
+// workspace and the last CTA to finish a tile of the item adds them in unit
+// order.  Every result is independent of scheduling (bit-identical run to run,
+// alone or in any batch with the same tile shape).
 #pragma once
 #include "nurbs_basis.cuh"
 #include "nurbs_tables.h"
@@ -36,8 +39,6 @@ enum : unsigned {
     kErrOrder = 1u << 5,
 };
 
-constexpr int kMaxBasis = 8;    // basis table stride: (max degree + 1) rounded up to a float4 pair
-constexpr int kMaxKnotWin = 10; // 2 * max degree
 constexpr int kRing = 8;        // rows of dL/dS (or target) in flight per warp (power of two)
 constexpr int kBatch = 4;       // retired control rows contracted together
 constexpr int kJbCap = 256;     // column ranges cached per tile
