@@ -134,3 +134,71 @@ class PerItemEngine:
         for k, p in enumerate(self.plans):
             p.mse_fwd_bwd(e.knots, e.ctrl, e.params, e.target, e.pts, e.grad_ctrl, e.grad_knots, e.loss[k:],
                           e.grad_scale)
+
+
+class StreamedSteps:
+    """Fused MSE steps fed from pinned host memory, with the copies overlapped.
+
+    Each step copies its inputs (knots, control net, samples, target) host to
+    device, runs the fused forward + MSE + backward, and copies its results
+    (control-point and knot gradients, per-item loss) back.  Two device buffer
+    sets alternate.  Step k's inputs go in on one stream while step k-1 computes
+    on another and step k-2's results come back on a third, so a run of steps
+    costs about max(copy in, compute + copy out) per step instead of their sum.
+    """
+
+    IN = ("knots", "ctrl", "params", "target")
+    OUT = ("grad_ctrl", "grad_knots", "loss")
+
+    def __init__(self, plan: batch.Plan, host_in: dict, host_out: dict, grad_scale: float, device="cuda"):
+        self.plan = plan
+        self.dev = torch.device(device)
+        self.host_in, self.host_out = host_in, host_out
+        self.grad_scale = float(grad_scale)
+        self.bufs = []
+        for _ in range(2):
+            b = {k: torch.empty_like(host_in[k], device=self.dev) for k in self.IN}
+            b.update({k: torch.empty_like(host_out[k], device=self.dev) for k in self.OUT})
+            self.bufs.append(b)
+        self.pts = torch.empty((max(plan.points, 1), 3), device=self.dev)
+        self.s_in = torch.cuda.Stream(self.dev)
+        self.s_cmp = torch.cuda.Stream(self.dev)
+        self.s_out = torch.cuda.Stream(self.dev)
+        self.ev_in = [torch.cuda.Event() for _ in range(2)]
+        self.ev_cmp = [torch.cuda.Event() for _ in range(2)]
+        self.ev_out = [torch.cuda.Event() for _ in range(2)]
+        self.k = 0
+
+    def step(self):
+        b = self.k % 2
+        buf = self.bufs[b]
+        if self.k >= 2:
+            self.s_in.wait_event(self.ev_cmp[b])        # step k-2 no longer reads these inputs
+        with torch.cuda.stream(self.s_in):
+            for key in self.IN:
+                buf[key].copy_(self.host_in[key], non_blocking=True)
+        self.ev_in[b].record(self.s_in)
+        self.s_cmp.wait_event(self.ev_in[b])
+        if self.k >= 2:
+            self.s_cmp.wait_event(self.ev_out[b])       # step k-2's results have left these buffers
+        self.plan.mse_fwd_bwd(buf["knots"], buf["ctrl"], buf["params"], buf["target"], self.pts,
+                              buf["grad_ctrl"], buf["grad_knots"], buf["loss"], self.grad_scale, stream=self.s_cmp)
+        self.ev_cmp[b].record(self.s_cmp)
+        self.s_out.wait_event(self.ev_cmp[b])
+        with torch.cuda.stream(self.s_out):
+            for key in self.OUT:
+                self.host_out[key].copy_(buf[key], non_blocking=True)
+        self.ev_out[b].record(self.s_out)
+        self.k += 1
+
+    def run(self, steps: int):
+        """Issue `steps` steps; returns the (start, end) events around them
+        (start on the input stream, end after the last result copy)."""
+        start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        self.s_in.wait_stream(torch.cuda.current_stream(self.dev))
+        start.record(self.s_in)
+        for _ in range(steps):
+            self.step()
+        self.s_out.wait_stream(self.s_cmp)
+        end.record(self.s_out)
+        return start, end

@@ -105,3 +105,27 @@ def test_server_results_same_alone_and_in_the_mix():
         assert all(last[m] < first[m] for m in mids[4:])
     finally:
         srv.stop()
+
+
+def test_streamed_steps_match_direct_step():
+    surfs, targets = synth.bicubic_batch(44, batch=5, net=10, grid=33)
+    pk, tk = batch.pack_surfaces(surfs), batch.pack_surfaces(targets)
+    kn, ct, pr = batch.to_device(pk)
+    _, tct, _ = batch.to_device(tk)
+    plan = batch.Plan.for_packed(pk)
+    T = torch.empty((pk.npts, 3), device="cuda")
+    batch.Plan.for_packed(tk).eval(kn, tct, pr, T)
+    scale = 2.0 / (3.0 * pk.npts)
+    gc, gk, loss = torch.empty_like(ct), torch.empty_like(kn), torch.empty(pk.count, device="cuda")
+    plan.mse_fwd_bwd(kn, ct, pr, T, None, gc, gk, loss, scale)
+    host_in = {"knots": kn.cpu().pin_memory(), "ctrl": ct.cpu().pin_memory(), "params": pr.cpu().pin_memory(),
+               "target": T.cpu().pin_memory()}
+    host_out = {"grad_ctrl": torch.empty_like(gc, device="cpu").pin_memory(),
+                "grad_knots": torch.empty_like(gk, device="cpu").pin_memory(),
+                "loss": torch.empty_like(loss, device="cpu").pin_memory()}
+    runner = engine.StreamedSteps(plan, host_in, host_out, scale)
+    _, end = runner.run(5)
+    end.synchronize()
+    assert torch.equal(host_out["grad_ctrl"], gc.cpu())
+    assert torch.equal(host_out["grad_knots"], gk.cpu())
+    assert torch.equal(host_out["loss"], loss.cpu())
