@@ -444,7 +444,6 @@ def bench_ragged(dev, steps, warmup, flush, peak, count=1000):
     """1000 surfaces, degrees 2..5, nets 8..64 and grids 32..256 per direction:
     fwd + MSE + bwd through the CUDA-graph engine, against one launch per surface."""
     import torch
-    from oracle import oracle as O  # noqa: F401  (targets come from the GPU forward below)
     from paper_2104_14547_gb300 import batch, engine, synth
     surfs, targets = synth.ragged_batch(0, count)
     pk = batch.pack_surfaces(surfs)
@@ -478,7 +477,6 @@ def bench_ragged(dev, steps, warmup, flush, peak, count=1000):
 def bench_serve(dev, rates=(1000, 2000, 5000, 10000, 20000, 50000), n_requests=20000, seeds=None):
     """Poisson streams of evaluate / fit-step requests on device-resident models
     shaped like the ragged workload; p50/p99 latency and throughput per rate."""
-    from oracle import oracle as O  # noqa: F401
     from paper_2104_14547_gb300 import batch, serve, synth
     import torch
     surfs, targets = synth.ragged_batch(7, 512)
