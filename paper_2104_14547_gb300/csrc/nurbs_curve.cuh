@@ -259,7 +259,9 @@ __device__ __forceinline__ void curve_body(const KParams& kp, int t, unsigned ch
         const float* rb = s_ring + ((k & (kCurveStages - 1)) * 32 + lane) * 16;
         const int bb = b0 + k * R;
         // target word w = 3j + c of the round sits in chunk 1 + w / 4
-#pragma unroll
+        // one copy of the per-sample body (unrolling it four times costs more in
+        // instruction fetch than it saves)
+#pragma unroll 1
         for (int j = 0; j < R; ++j) {
             if (bb + j < b1) {
                 float g[3] = {0.f, 0.f, 0.f};
