@@ -94,6 +94,7 @@ class Adam(ctypes.Structure):
 
 
 KIND_SURFACE, KIND_CURVE = 0, 1
+ERR_SIZE = 8   # NURBS_ERR_SIZE: an item or tile shape exceeds a kernel limit
 
 # every function the header declares, with its ctypes signature
 _vp, _f, _i32, _i64, _sz = ctypes.c_void_p, ctypes.c_float, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t

@@ -12,9 +12,9 @@ import hashlib
 import numpy as np
 import torch
 
-from . import batch
+from . import _lib, batch
 
-DEFAULT_CANDIDATES = [(8, 32), (8, 64), (8, 128), (4, 32), (4, 64), (4, 128), (2, 32)]
+DEFAULT_CANDIDATES = [(8, 32), (8, 64), (8, 128), (8, 256), (4, 32), (4, 64), (4, 128), (4, 256), (2, 32)]
 _cache: dict = {}
 
 
@@ -66,10 +66,18 @@ def autotune(packed: batch.Packed, tensors: dict, op: str = "mse", candidates=No
             fn = lambda: plan.mse_fwd_bwd(kn, ct, pr, tensors["target"], tensors.get("pts"),
                                           tensors.get("grad_ctrl"), tensors.get("grad_knots"),
                                           tensors.get("loss"))
-        fn()
+        try:
+            fn()
+        except _lib.NurbsError as e:
+            if e.status != _lib.ERR_SIZE:      # a shape the kernels cannot hold is skipped
+                raise
+            del plan
+            continue
         torch.cuda.synchronize()
         table[(warps, rows)] = _time(fn, reps, flush)
         del plan
+    if not table:
+        raise RuntimeError("no candidate tile shape fits this batch")
     best = min(table, key=table.get)
     _cache[key] = (best, table)
     return best, table
