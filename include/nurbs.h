@@ -283,6 +283,12 @@ nurbs_status nurbs_mse_fwd_bwd_noalloc(const nurbs_plan* plan, const float* knot
  *                       distance to it.  nn_q, dist_q: the same for Q.
  *   cd, hd              optional outputs, one per pair.
  *   grad_cd, grad_hd    optional outputs, [n][3] like P: gradients of L_CD and L_HD.
+ *   scratch             optional: 2*total_p + total_q int32 of device scratch
+ *                       (total_p = p_off[count], total_q = q_off[count]).  With it,
+ *                       the Chamfer gradient buckets the Q points by nearest P point
+ *                       (O(n + m) per pair).  Without it, each P point scans its
+ *                       pair's whole nearest-point map (O(n m)).  The results are
+ *                       the same.
  * Nearest points are decided on float32 squared distances, each rounded as
  * ((dx dx + dy dy) + dz dz); ties go to the first index.  A zero distance
  * contributes no gradient.  A pair with an empty side gives 0 and zero
@@ -293,7 +299,7 @@ nurbs_status nurbs_mse_fwd_bwd_noalloc(const nurbs_plan* plan, const float* knot
 nurbs_status nurbs_chamfer(int32_t count, const int64_t* p_off, const int64_t* q_off, int32_t max_p, int32_t max_q,
                            const float* P, const float* Q, int32_t* nn_p, float* dist_p, int32_t* nn_q,
                            float* dist_q, float* cd, float* hd, float* grad_cd, float* grad_hd,
-                           nurbs_stream_t stream);
+                           int32_t* scratch, int64_t total_p, int64_t total_q, nurbs_stream_t stream);
 
 /* Human-readable name of a status code (static string). */
 const char* nurbs_status_string(nurbs_status status);

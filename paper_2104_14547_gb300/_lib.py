@@ -116,7 +116,8 @@ SIGNATURES = {
     "nurbs_mse_fwd_bwd": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _f, _vp]),
     "nurbs_mse_fwd_bwd_noalloc": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _f, _vp]),
     "nurbs_fit_step": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.POINTER(Adam), _i32, _f, _vp, _vp, _vp]),
-    "nurbs_chamfer": (_i32, [_i32, _vp, _vp, _i32, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "nurbs_chamfer": (_i32, [_i32, _vp, _vp, _i32, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
+                             _i64, _i64, _vp]),
     "nurbs_status_string": (ctypes.c_char_p, [_i32]),
     "nurbs_last_cuda_error": (_i32, []),
 }

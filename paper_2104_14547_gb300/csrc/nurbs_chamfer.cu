@@ -14,8 +14,12 @@
 //   reduce_kernel  one CTA per pair: sums and maxima in a fixed order, and the
 //                  Hausdorff gradient at the two arg-max points.
 //   grad_kernel    the Chamfer gradient of every P_i: its own term, then the
-//                  terms of the Q_j whose nearest point it is, in j order (no
-//                  atomics; deterministic).
+//                  terms of the Q_j whose nearest point it is, in j order.
+//                  With scratch, the Q points are first bucketed by their
+//                  nearest P point: integer counts, a per-pair prefix sum, and
+//                  placement, then each bucket is sorted by j, so the sums keep a
+//                  fixed order.  Without scratch, each P_i scans the pair's whole
+//                  nearest-point map instead.
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -188,12 +192,115 @@ __global__ void __launch_bounds__(kThreads) grad_kernel(const float* __restrict_
     }
 }
 
+
+// ---- bucketing of the Q points by their nearest P point (scratch path)
+__global__ void __launch_bounds__(kThreads) count_kernel(const int64_t* __restrict__ p_off,
+                                                         const int64_t* __restrict__ q_off,
+                                                         const int32_t* __restrict__ nn_q, int32_t* __restrict__ cnt)
+{
+    const int k = blockIdx.y;
+    const long long p0 = p_off[k], q0 = q_off[k], nq = q_off[k + 1] - q0;
+    for (long long j = (long long)blockIdx.x * kThreads + threadIdx.x; j < nq; j += (long long)gridDim.x * kThreads) {
+        const int i = nn_q[q0 + j];
+        if (i >= 0) atomicAdd(cnt + p0 + i, 1);   // integer counts: the result does not depend on order
+    }
+}
+
+// Per pair: start[i] = q0 + exclusive prefix of the counts; cursor[i] = start[i].
+__global__ void __launch_bounds__(kThreads) scan_kernel(const int64_t* __restrict__ p_off,
+                                                        const int64_t* __restrict__ q_off,
+                                                        int32_t* __restrict__ start, int32_t* __restrict__ cursor)
+{
+    __shared__ int32_t s_v[kThreads];
+    const int k = blockIdx.x;
+    const long long p0 = p_off[k], np = p_off[k + 1] - p0;
+    int32_t carry = (int32_t)q_off[k];
+    for (long long c0 = 0; c0 < np; c0 += kThreads) {
+        const long long i = c0 + threadIdx.x;
+        const int32_t v = i < np ? cursor[p0 + i] : 0;   // the counts
+        s_v[threadIdx.x] = v;
+        __syncthreads();
+        for (int o = 1; o < kThreads; o <<= 1) {          // inclusive Hillis-Steele scan
+            const int32_t add = threadIdx.x >= o ? s_v[threadIdx.x - o] : 0;
+            __syncthreads();
+            s_v[threadIdx.x] += add;
+            __syncthreads();
+        }
+        if (i < np) {
+            const int32_t st = carry + s_v[threadIdx.x] - v;
+            start[p0 + i] = st;
+            cursor[p0 + i] = st;
+        }
+        carry += s_v[kThreads - 1];
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) place_kernel(const int64_t* __restrict__ p_off,
+                                                         const int64_t* __restrict__ q_off,
+                                                         const int32_t* __restrict__ nn_q, int32_t* __restrict__ cursor,
+                                                         int32_t* __restrict__ list)
+{
+    const int k = blockIdx.y;
+    const long long p0 = p_off[k], q0 = q_off[k], nq = q_off[k + 1] - q0;
+    for (long long j = (long long)blockIdx.x * kThreads + threadIdx.x; j < nq; j += (long long)gridDim.x * kThreads) {
+        const int i = nn_q[q0 + j];
+        if (i >= 0) list[atomicAdd(cursor + p0 + i, 1)] = (int32_t)j;   // order fixed later by sorting
+    }
+}
+
+// Chamfer gradient from the buckets: P_i's own term, then its bucket in j order.
+__global__ void __launch_bounds__(kThreads) grad_bucket_kernel(const float* __restrict__ P,
+                                                               const int64_t* __restrict__ p_off,
+                                                               const float* __restrict__ Q,
+                                                               const int64_t* __restrict__ q_off,
+                                                               const int32_t* __restrict__ nn_p,
+                                                               const float* __restrict__ d_p,
+                                                               const float* __restrict__ d_q,
+                                                               const int32_t* __restrict__ start,
+                                                               const int32_t* __restrict__ end, int32_t* list,
+                                                               float* __restrict__ grad_cd)
+{
+    const int k = blockIdx.y;
+    const long long p0 = p_off[k], np = p_off[k + 1] - p0, q0 = q_off[k], nq = q_off[k + 1] - q0;
+    const long long i = (long long)blockIdx.x * kThreads + threadIdx.x;
+    if (i >= np) return;
+    float gx = 0.f, gy = 0.f, gz = 0.f;
+    if (nq > 0) {
+        const float4 pi = load3(P, p0 + i);
+        const float d = d_p[p0 + i];
+        if (d > 0.f) {
+            const float4 q = load3(Q, q0 + nn_p[p0 + i]);
+            gx = (pi.x - q.x) / d; gy = (pi.y - q.y) / d; gz = (pi.z - q.z) / d;
+        }
+        const int a = start[p0 + i], b = end[p0 + i];
+        for (int x = a + 1; x < b; ++x) {                 // insertion sort of the bucket by j
+            const int v = list[x];
+            int y = x - 1;
+            while (y >= a && list[y] > v) { list[y + 1] = list[y]; --y; }
+            list[y + 1] = v;
+        }
+        for (int x = a; x < b; ++x) {
+            const long long j = q0 + list[x];
+            const float dj = d_q[j];
+            if (dj > 0.f) {
+                const float4 q = load3(Q, j);
+                gx += (pi.x - q.x) / dj; gy += (pi.y - q.y) / dj; gz += (pi.z - q.z) / dj;
+            }
+        }
+    }
+    grad_cd[3 * (p0 + i)] = gx;
+    grad_cd[3 * (p0 + i) + 1] = gy;
+    grad_cd[3 * (p0 + i) + 2] = gz;
+}
+
 }  // namespace
 
 extern "C" nurbs_status nurbs_chamfer(int32_t count, const int64_t* p_off, const int64_t* q_off, int32_t max_p,
                                       int32_t max_q, const float* P, const float* Q, int32_t* nn_p, float* dist_p,
                                       int32_t* nn_q, float* dist_q, float* cd, float* hd, float* grad_cd,
-                                      float* grad_hd, nurbs_stream_t stream)
+                                      float* grad_hd, int32_t* scratch, int64_t total_p, int64_t total_q,
+                                      nurbs_stream_t stream)
 {
     if (count < 0 || max_p < 0 || max_q < 0) return NURBS_ERR_ARG;
     if (count == 0) return NURBS_OK;
@@ -210,8 +317,23 @@ extern "C" nurbs_status nurbs_chamfer(int32_t count, const int64_t* p_off, const
     if (cd != nullptr || hd != nullptr || grad_hd != nullptr)
         reduce_kernel<<<count, kThreads, 0, s>>>(P, p_off, Q, q_off, nn_p, dist_p, nn_q, dist_q, cd, hd, grad_hd);
     const unsigned gp = (unsigned)((max_p + kThreads - 1) / kThreads);
-    if (grad_cd != nullptr && gp > 0)
-        grad_kernel<<<dim3(gp, count), kThreads, 0, s>>>(P, p_off, Q, q_off, nn_p, dist_p, nn_q, dist_q, grad_cd);
+    if (grad_cd != nullptr && gp > 0) {
+        if (scratch != nullptr && total_p > 0) {
+            int32_t* start = scratch;
+            int32_t* cursor = scratch + total_p;
+            int32_t* list = scratch + 2 * total_p;
+            const cudaError_t e0 = cudaMemsetAsync(cursor, 0, sizeof(int32_t) * (size_t)total_p, s);
+            if (e0 != cudaSuccess) return NURBS_ERR_CUDA;
+            const unsigned gq = (unsigned)min((max_q + kThreads - 1) / kThreads, 64);
+            if (gq > 0) count_kernel<<<dim3(gq, count), kThreads, 0, s>>>(p_off, q_off, nn_q, cursor);
+            scan_kernel<<<count, kThreads, 0, s>>>(p_off, q_off, start, cursor);
+            if (gq > 0) place_kernel<<<dim3(gq, count), kThreads, 0, s>>>(p_off, q_off, nn_q, cursor, list);
+            grad_bucket_kernel<<<dim3(gp, count), kThreads, 0, s>>>(P, p_off, Q, q_off, nn_p, dist_p, dist_q, start,
+                                                                    cursor, list, grad_cd);
+        } else {
+            grad_kernel<<<dim3(gp, count), kThreads, 0, s>>>(P, p_off, Q, q_off, nn_p, dist_p, nn_q, dist_q, grad_cd);
+        }
+    }
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? NURBS_OK : NURBS_ERR_CUDA;
 }

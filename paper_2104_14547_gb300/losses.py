@@ -15,11 +15,13 @@ def _ptr(t):
     return None if t is None else ctypes.c_void_p(t.data_ptr())
 
 
-def chamfer(P: torch.Tensor, p_sizes, Q: torch.Tensor, q_sizes, grad: bool = True, stream=None):
+def chamfer(P: torch.Tensor, p_sizes, Q: torch.Tensor, q_sizes, grad: bool = True, stream=None,
+            bucketed: bool = True):
     """P [sum(p_sizes), 3] and Q [sum(q_sizes), 3] float32 CUDA tensors, split into
     pairs by the sizes.  Returns a dict with per-pair "cd", "hd", per-point
     "grad_cd", "grad_hd" (when grad), and the nearest-point maps "nn_p", "nn_q"
-    with distances "dist_p", "dist_q"."""
+    with distances "dist_p", "dist_q".  bucketed=False takes the O(n m) gradient
+    path (the same results, no scratch)."""
     dev = P.device
     p_sizes = np.asarray(p_sizes, np.int64)
     q_sizes = np.asarray(q_sizes, np.int64)
@@ -39,11 +41,12 @@ def chamfer(P: torch.Tensor, p_sizes, Q: torch.Tensor, q_sizes, grad: bool = Tru
         out["grad_cd"] = torch.empty((max(np_, 1), 3), device=dev)
         out["grad_hd"] = torch.empty((max(np_, 1), 3), device=dev)
     s = stream if stream is not None else torch.cuda.current_stream(dev)
+    scratch = torch.empty(2 * np_ + nq_ + 1, dtype=torch.int32, device=dev) if (grad and bucketed) else None
     lib = _lib.load()
     _lib.check(lib.nurbs_chamfer(count, _ptr(p_off), _ptr(q_off), int(p_sizes.max(initial=0)),
                                  int(q_sizes.max(initial=0)), _ptr(P), _ptr(Q), _ptr(out["nn_p"]),
                                  _ptr(out["dist_p"]), _ptr(out["nn_q"]), _ptr(out["dist_q"]), _ptr(out["cd"]),
                                  _ptr(out["hd"]), _ptr(out.get("grad_cd")), _ptr(out.get("grad_hd")),
-                                 ctypes.c_void_p(s.cuda_stream)), "nurbs_chamfer")
-    out["_keep"] = (p_off, q_off)   # the offsets stay alive until the stream has used them
+                                 _ptr(scratch), np_, nq_, ctypes.c_void_p(s.cuda_stream)), "nurbs_chamfer")
+    out["_keep"] = (p_off, q_off, scratch)   # these stay alive until the stream has used them
     return out

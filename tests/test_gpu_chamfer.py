@@ -32,10 +32,10 @@ def _pairs(seed):
     return Ps, Qs
 
 
-def _run(Ps, Qs):
+def _run(Ps, Qs, bucketed=True):
     P = torch.from_numpy(np.concatenate([p.reshape(-1, 3) for p in Ps])).cuda()
     Q = torch.from_numpy(np.concatenate([q.reshape(-1, 3) for q in Qs])).cuda()
-    out = losses.chamfer(P, [len(p) for p in Ps], Q, [len(q) for q in Qs])
+    out = losses.chamfer(P, [len(p) for p in Ps], Q, [len(q) for q in Qs], bucketed=bucketed)
     torch.cuda.synchronize()
     return {k: v.cpu().numpy() for k, v in out.items() if k != "_keep"}
 
@@ -60,11 +60,13 @@ def test_chamfer_matches_oracle():
         qa += m
 
 
-def test_chamfer_is_deterministic():
+def test_chamfer_is_deterministic_and_paths_agree():
     Ps, Qs = _pairs(41)
     a, b = _run(Ps, Qs), _run(Ps, Qs)
+    c = _run(Ps, Qs, bucketed=False)
     for key in ("cd", "hd", "grad_cd", "grad_hd", "nn_p", "nn_q"):
         np.testing.assert_array_equal(a[key], b[key])
+        np.testing.assert_array_equal(a[key], c[key])   # bucketed and scanning gradients: same bits
 
 
 def test_chamfer_of_evaluated_surfaces():

@@ -153,6 +153,18 @@ def test_backward_tile_shapes(warps, rows):
     _check_grads(items, SURF, pk, g, gc, gk)
 
 
+def test_backward_curves_repeated_knots():
+    rng = np.random.default_rng(18)
+    items = []
+    for p, n1, nu in ((3, 12, 400), (2, 300, 900)):         # curve kernels, then the tile kernels
+        c = synth.curve(rng, p, n1, nu, knots="uniform")
+        U = c.U.copy()
+        U[p + 3] = U[p + 4]                                 # a double interior knot
+        items.append(synth.Curve(p, U, c.ctrl, c.u))
+    pk, g, gc, gk = _run_backward(items, CURVE, 18)
+    _check_grads(items, CURVE, pk, g, gc, gk)
+
+
 def test_backward_curves():
     items = curves_mixed(8)
     pk, g, gc, gk = _run_backward(items, CURVE, 8)
@@ -165,7 +177,12 @@ def test_backward_edge_cases():
     one = synth.surface(rng, 2, 2, 5, 5, 1, 1)
     empty = synth.surface(rng, 3, 3, 6, 6, 0, 10)
     sparse = synth.surface(rng, 3, 2, 40, 30, 5, 4)       # samples jump over many spans
-    items = [onk, one, empty, sparse]
+    rep = synth.surface(rng, 2, 3, 8, 9, 50, 60)          # repeated interior knots: 0/0 := 0 in Eq. 4
+    rep.U = rep.U.copy()
+    rep.U[4] = rep.U[5]                                   # a double knot in u
+    rep.V = rep.V.copy()
+    rep.V[5] = rep.V[6] = rep.V[7]                        # a triple knot in v (C0 across it)
+    items = [onk, one, empty, sparse, rep]
     pk, g, gc, gk = _run_backward(items, SURF, 9)
     # sample-on-knot items: control/weight gradients are exact, knot gradients one-sided
     _check_grads(items, SURF, pk, g, gc, gk)
