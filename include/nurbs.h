@@ -146,6 +146,20 @@ void nurbs_plan_destroy(nurbs_plan* plan);
 nurbs_status nurbs_plan_set_knot_sigma(nurbs_plan* plan, float sigma);
 
 /*
+ * nurbs_plan_set_grad_homogeneous -- choose the parameterisation of the control
+ * point gradients that later backward, MSE and fit-step calls on this plan write
+ * to grad_ctrl (host only).
+ *   on == 0 (the default): the paper's parameters, (dL/dx, dL/dy, dL/dz, dL/dw)
+ *     for the Cartesian point P and its weight w (Eq. 7, Eq. 8).
+ *   on == 1: the homogeneous point Pw = (w x, w y, w z, w) of Eq. 3,
+ *     (dL/dPw.x, dL/dPw.y, dL/dPw.z, dL/dPw.w), related to the above by
+ *     dL/dPw.xyz = (dL/dP) / w and dL/dPw.w = dL/dw - P . (dL/dP) / w.
+ * nurbs_fit_step's Adam update always acts on (P, w).  Errors: NURBS_ERR_ARG for
+ * a null plan or `on` outside {0, 1}.
+ */
+nurbs_status nurbs_plan_set_grad_homogeneous(nurbs_plan* plan, int32_t on);
+
+/*
  * nurbs_plan_get_error -- synchronise `stream`, read and clear the device error
  * word written by the device-side checks of earlier calls.  *flags receives the
  * raw bit set (bit k set <=> status k was raised); returns the lowest raised
@@ -195,7 +209,8 @@ nurbs_status nurbs_eval_curve_derivs(const nurbs_plan* plan, const float* knots,
  * nurbs_backward -- vector-Jacobian product of the evaluation (Sec. 3.2, Eq. 7,
  * Eq. 8, Eq. 9, the knot derivative, Alg. 2), for surface or curve plans.
  *   grad_pts    dL/dS in the pts layout
- *   grad_ctrl   receives (dL/dx, dL/dy, dL/dz, dL/dw) per control point, or NULL
+ *   grad_ctrl   receives (dL/dx, dL/dy, dL/dz, dL/dw) per control point (or the
+ *               homogeneous form, see nurbs_plan_set_grad_homogeneous), or NULL
  *   grad_knots  receives dL/dU (and dL/dV), or NULL.  Knot gradients are the
  *               almost-everywhere derivative of the Cox-de Boor recursion (the
  *               sigma -> 0 limit of the smoothed indicator of Sec. 3.2); the

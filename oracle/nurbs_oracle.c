@@ -446,6 +446,75 @@ void nurbs_oracle_curve_vjp(int p, int n1, const double* U, const double* ctrl,
 }
 
 /* ---------------------------------------------------------------------------
+ * Gradients with respect to the homogeneous control points Pw = (w x, w y, w z, w)
+ * (the optional parameterisation of the library).  S = NR / W with NR and W
+ * linear in Pw (Eq. 3 written homogeneously), so
+ *   dS/dPw.xyz_ij = N_i N_j / W (identity on xyz),  dS/dPw.w_ij = -N_i N_j S / W.
+ * dpw[i][j][4] = (dL/dPw.x, dL/dPw.y, dL/dPw.z, dL/dPw.w).
+ */
+void nurbs_oracle_surface_vjp_homog(int p, int q, int n1, int m1, const double* U, const double* V,
+                                    const double* ctrl, int nu, const double* u, int nv, const double* v,
+                                    const double* g, double* dpw)
+{
+    memset(dpw, 0, sizeof(double) * 4 * (size_t)n1 * m1);
+    double Nu[OR_MAXDEG + 1], Nv[OR_MAXDEG + 1];
+    for (int a = 0; a < nu; ++a) {
+        int su = nurbs_oracle_find_span(n1 - 1, p, u[a], U);
+        nurbs_oracle_basis_funs(su, u[a], p, U, Nu);
+        for (int b = 0; b < nv; ++b) {
+            int sv = nurbs_oracle_find_span(m1 - 1, q, v[b], V);
+            nurbs_oracle_basis_funs(sv, v[b], q, V, Nv);
+            double NR[3] = {0, 0, 0}, W = 0;
+            for (int r = 0; r <= p; ++r)
+                for (int h = 0; h <= q; ++h) {
+                    const double* c = ctrl + 4 * ((size_t)(su - p + r) * m1 + (sv - q + h));
+                    double bw = Nu[r] * Nv[h] * c[3];
+                    NR[0] += bw * c[0]; NR[1] += bw * c[1]; NR[2] += bw * c[2];
+                    W += bw;
+                }
+            const double* ga = g + 3 * ((size_t)a * nv + b);
+            double Sg = (NR[0] * ga[0] + NR[1] * ga[1] + NR[2] * ga[2]) / W;
+            for (int r = 0; r <= p; ++r)
+                for (int h = 0; h <= q; ++h) {
+                    double* d = dpw + 4 * ((size_t)(su - p + r) * m1 + (sv - q + h));
+                    double NN = Nu[r] * Nv[h];
+                    d[0] += NN * ga[0] / W;
+                    d[1] += NN * ga[1] / W;
+                    d[2] += NN * ga[2] / W;
+                    d[3] -= NN * Sg / W;
+                }
+        }
+    }
+}
+
+void nurbs_oracle_curve_vjp_homog(int p, int n1, const double* U, const double* ctrl,
+                                  int nu, const double* u, const double* g, double* dpw)
+{
+    memset(dpw, 0, sizeof(double) * 4 * (size_t)n1);
+    double N[OR_MAXDEG + 1];
+    for (int a = 0; a < nu; ++a) {
+        int s = nurbs_oracle_find_span(n1 - 1, p, u[a], U);
+        nurbs_oracle_basis_funs(s, u[a], p, U, N);
+        double NR[3] = {0, 0, 0}, W = 0;
+        for (int r = 0; r <= p; ++r) {
+            const double* c = ctrl + 4 * (s - p + r);
+            double bw = N[r] * c[3];
+            NR[0] += bw * c[0]; NR[1] += bw * c[1]; NR[2] += bw * c[2];
+            W += bw;
+        }
+        const double* ga = g + 3 * a;
+        double Sg = (NR[0] * ga[0] + NR[1] * ga[1] + NR[2] * ga[2]) / W;
+        for (int r = 0; r <= p; ++r) {
+            double* d = dpw + 4 * (s - p + r);
+            d[0] += N[r] * ga[0] / W;
+            d[1] += N[r] * ga[1] / W;
+            d[2] += N[r] * ga[2] / W;
+            d[3] -= N[r] * Sg / W;
+        }
+    }
+}
+
+/* ---------------------------------------------------------------------------
  * Parametric derivatives (the u-derivative of Eq. 4, for the surface tangents
  * and normals the paper's offsetting application uses, Sec. 3.1 and Sec. 4).
  *

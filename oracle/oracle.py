@@ -13,6 +13,7 @@ inputs the GPU path sees) and calls the C routine of the same role:
 * ``basis_knot_jac_sigma``            -- the same with the Gaussian-smoothed indicator term
 * ``surface_eval`` / ``curve_eval``   -- Eq. 3 (and its one-direction form)
 * ``surface_vjp`` / ``curve_vjp``     -- Eq. 7, Eq. 8, Eq. 9 + knot derivative
+* ``surface_vjp_homog`` / ``curve_vjp_homog`` -- gradient w.r.t. homogeneous Pw (Eq. 3)
 * ``basis_ders``                      -- u-derivative of the nonzero basis (of Eq. 4)
 * ``surface_derivs`` / ``curve_derivs`` -- tangents S_u, S_v, unit normals (curve: C')
 * ``mse``, ``adam``                   -- the L2 (MSE) loss and the Adam step of Sec. 4
@@ -66,6 +67,8 @@ def lib():
             L.nurbs_oracle_basis_knot_jac_sigma.argtypes = [i, d, i, _D, d, _D, _D]
             L.nurbs_oracle_curve_eval.argtypes = [i, i, _D, _D, i, _D, _D]
             L.nurbs_oracle_curve_vjp.argtypes = [i, i, _D, _D, i, _D, _D, _D, _D]
+            L.nurbs_oracle_surface_vjp_homog.argtypes = [i, i, i, i, _D, _D, _D, i, _D, i, _D, _D, _D]
+            L.nurbs_oracle_curve_vjp_homog.argtypes = [i, i, _D, _D, i, _D, _D, _D]
             L.nurbs_oracle_basis_ders.argtypes = [i, d, i, _D, _D]
             L.nurbs_oracle_surface_derivs.argtypes = [i, i, i, i, _D, _D, _D, i, _D, i, _D, _D, _D, _D, _D]
             L.nurbs_oracle_curve_derivs.argtypes = [i, i, _D, _D, i, _D, _D, _D]
@@ -148,6 +151,18 @@ def surface_vjp(p, q, U, V, ctrl, u, v, g, want_ctrl=True, want_knots=True, knot
     return dctrl, dU, dV
 
 
+def surface_vjp_homog(p, q, U, V, ctrl, u, v, g):
+    """dL/dPw[n1, m1, 4] for the homogeneous control points Pw = (w x, w y, w z, w)."""
+    ctrl = _f64(ctrl)
+    n1, m1 = ctrl.shape[0], ctrl.shape[1]
+    U, V, u, v, g = _f64(U), _f64(V), _f64(u), _f64(v), _f64(g)
+    assert g.shape == (len(u), len(v), 3)
+    dpw = np.zeros((n1, m1, 4))
+    lib().nurbs_oracle_surface_vjp_homog(p, q, n1, m1, _p(U), _p(V), _p(ctrl), len(u), _p(u), len(v), _p(v),
+                                         _p(g), _p(dpw))
+    return dpw
+
+
 # --------------------------------------------------------------------- curve
 def curve_eval(p, U, ctrl, u) -> np.ndarray:
     ctrl = _f64(ctrl)
@@ -168,6 +183,15 @@ def curve_vjp(p, U, ctrl, u, g, want_ctrl=True, want_knots=True, knot_sigma=0.0)
     lib().nurbs_oracle_curve_vjp_sigma(p, n1, _p(U), _p(ctrl), len(u), _p(u), _p(g), _p(dctrl), _p(dU),
                                        float(knot_sigma))
     return dctrl, dU
+
+
+def curve_vjp_homog(p, U, ctrl, u, g):
+    ctrl = _f64(ctrl)
+    n1 = ctrl.shape[0]
+    U, u, g = _f64(U), _f64(u), _f64(g)
+    dpw = np.zeros((n1, 4))
+    lib().nurbs_oracle_curve_vjp_homog(p, n1, _p(U), _p(ctrl), len(u), _p(u), _p(g), _p(dpw))
+    return dpw
 
 
 # ----------------------------------------------------------------- loss, adam

@@ -175,6 +175,12 @@ class Plan:
         > 0 = the Gaussian-smoothed indicator of bandwidth sigma."""
         _lib.check(self.lib.nurbs_plan_set_knot_sigma(self.handle, ctypes.c_float(sigma)), "nurbs_plan_set_knot_sigma")
 
+    def set_grad_homogeneous(self, on: bool):
+        """Control-point gradients of later calls: False = (dL/dP, dL/dw) (default),
+        True = dL/dPw for Pw = (w x, w y, w z, w).  Adam in fit_step acts on (P, w) either way."""
+        _lib.check(self.lib.nurbs_plan_set_grad_homogeneous(self.handle, int(bool(on))),
+                   "nurbs_plan_set_grad_homogeneous")
+
     def eval_derivs(self, knots, ctrl, params, pts=None, du=None, dv=None, normals=None, stream=None):
         """Points with tangents and unit normals (surfaces: du, dv, normals; curves:
         the tangent goes to ``du``).  Outputs that are None are not written."""

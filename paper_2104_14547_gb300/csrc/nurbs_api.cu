@@ -59,6 +59,7 @@ struct nurbs_plan {
     int smem_eval;            // forward kernels (no shared adjoint)
     int c_mc, c_wbytes, c_smem;   // curve kernels: control capacity, bytes per warp, per CTA
     float knot_sigma;             // smoothed-indicator knot derivative bandwidth (0: off)
+    int grad_homog;               // control-point gradients with respect to Pw
     // workspace layout (bytes)
     size_t items_off, tiles_off, counts_off, part_off, ws_bytes;
     // binding
@@ -310,6 +311,13 @@ nurbs_status nurbs_plan_set_knot_sigma(nurbs_plan* plan, float sigma)
     plan->knot_sigma = sigma;
     return NURBS_OK;
 }
+
+nurbs_status nurbs_plan_set_grad_homogeneous(nurbs_plan* plan, int32_t on)
+{
+    if (plan == nullptr || (on != 0 && on != 1)) return NURBS_ERR_ARG;
+    plan->grad_homog = on;
+    return NURBS_OK;
+}
 int64_t nurbs_plan_points(const nurbs_plan* plan) { return plan ? plan->points : 0; }
 int32_t nurbs_plan_tiles(const nurbs_plan* plan) { return plan ? (int32_t)plan->tiles.size() : 0; }
 
@@ -423,6 +431,7 @@ void fill_tables(KParams& kp, const nurbs_plan* pl, unsigned char* ws)
     kp.c_mc = pl->c_mc;
     kp.c_wbytes = pl->c_wbytes;
     kp.knot_sigma = pl->knot_sigma;
+    kp.grad_homog = pl->grad_homog;
 }
 
 // Launch variant v (0 forward, 1/2 backward from dL/dS without/with knots, 3/4 the

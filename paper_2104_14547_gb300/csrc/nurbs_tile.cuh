@@ -79,6 +79,7 @@ struct KParams {
     float* d_nrm;
     int c_mc, c_wbytes;      // curve kernels: control-point capacity, shared bytes per warp
     float knot_sigma;        // > 0: knot derivative with the Gaussian-smoothed indicator term
+    int grad_homog;          // grad_ctrl receives dL/dPw (homogeneous) instead of dL/d(P, w)
 };
 
 __device__ __forceinline__ float4 f4zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
@@ -206,15 +207,16 @@ __device__ __forceinline__ void adam_corrections(const KParams& kp, const ItemDe
     }
 }
 
-// Control point idx (Cartesian c) from its homogeneous adjoint a: Cartesian
-// gradient and, in a fit step, the Adam update of the point, its weight and the
+// Control point idx (Cartesian c) from its homogeneous adjoint a = dL/dPw: the
+// gradient (Cartesian, or a itself when grad_homog is set) and, in a fit step, the
+// Adam update of the point and its weight from the Cartesian gradient, with the
 // moments mm, vv (loaded by the caller).
 __device__ __forceinline__ void finish_point(const KParams& kp, long long idx, float4 c, float4 a, float4 mm,
                                              float4 vv, float lr_t, float isb2)
 {
     // Pw = (w x, w y, w z, w): dL/dx = w A.x, ..., dL/dw = x A.x + y A.y + z A.z + A.w
     const float4 g = make_float4(c.w * a.x, c.w * a.y, c.w * a.z, fmaf(c.x, a.x, fmaf(c.y, a.y, fmaf(c.z, a.z, a.w))));
-    if (kp.grad_ctrl != nullptr) kp.grad_ctrl[idx] = g;
+    if (kp.grad_ctrl != nullptr) kp.grad_ctrl[idx] = kp.grad_homog ? a : g;
     if (kp.fit) {
         const float ob1 = 1.f - kp.b1, ob2 = 1.f - kp.b2;
         mm.x = fmaf(kp.b1, mm.x, ob1 * g.x); vv.x = fmaf(kp.b2, vv.x, ob2 * g.x * g.x);

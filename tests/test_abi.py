@@ -106,3 +106,17 @@ def test_knot_sigma_setter_validates():
     assert lib.nurbs_plan_set_knot_sigma(h, float("inf")) == 1
     assert lib.nurbs_plan_set_knot_sigma(None, 1e-3) == 1
     lib.nurbs_plan_destroy(h)
+
+
+def test_grad_homogeneous_setter_validates():
+    s = synth.single_bicubic(0)
+    pk = batch.pack_surfaces([s])
+    st, h = _plan(_lib.KIND_SURFACE, pk.descs)
+    assert st == 0
+    lib = _lib.load()
+    assert lib.nurbs_plan_set_grad_homogeneous(h, 1) == 0
+    assert lib.nurbs_plan_set_grad_homogeneous(h, 0) == 0
+    assert lib.nurbs_plan_set_grad_homogeneous(h, 2) == 1
+    assert lib.nurbs_plan_set_grad_homogeneous(h, -1) == 1
+    assert lib.nurbs_plan_set_grad_homogeneous(None, 1) == 1
+    lib.nurbs_plan_destroy(h)
