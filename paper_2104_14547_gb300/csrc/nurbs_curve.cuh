@@ -167,14 +167,14 @@ __device__ __forceinline__ void curve_body(const KParams& kp, int t, unsigned ch
         if (kk > pm + P) s_K[kk] = v;
         else if (kk - klo < KW) s_Kov[lane * KW + (kk - klo)] = v;
     };
+    // the window starts at the span of the lane's first sample
+    if (act) {
+#pragma unroll
+        for (int r = 0; r < PB; ++r) Qw[r] = homog(s_net[sf - P + r]);
+        cur = sf;
+    }
     // move the window to span s (s >= cur): retire what leaves, load what enters
     auto advance = [&](int s) {
-        if (cur < 0) {
-#pragma unroll
-            for (int r = 0; r < PB; ++r) Qw[r] = homog(s_net[s - P + r]);
-            cur = s;
-            return;
-        }
         while (cur < s) {
             if constexpr (GRAD) {
                 retire_row(cur - P, tau[0]);
@@ -200,7 +200,14 @@ __device__ __forceinline__ void curve_body(const KParams& kp, int t, unsigned ch
         if (u < uprev) err |= kErrOrder;
         uprev = u;
         u = fminf(fmaxf(u, ulo), uhi);
-        int s = cur < 0 ? sf : cur;
+        // The samples are non-decreasing, so the span only moves forward, mostly by
+        // one knot: step it a few knots (the same largest k with U_k <= u) before
+        // falling back to the binary search.  Lanes change span at different
+        // samples, so whatever this costs, the warp pays at almost every sample.
+        int s = cur;
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+            if (s < n && !(u < s_kn[s + 1])) ++s;
         if (s < n && !(u < s_kn[s + 1])) s = find_span(n, P, u, s_kn);
         advance(s);
         float N[PB];
