@@ -248,7 +248,7 @@ def run_ours(args):
     xs = max(5, args.steps // 2)
     if rank == 0 and not args.no_extra:
         if "curves" in want:
-            extras["curves_fit_step"] = bench_curves(dev, xs, args.warmup, flush, peak)
+            extras["curves_fit_step"], extras["curves_eval"] = bench_curves(dev, xs, args.warmup, flush, peak)
         if "derivs" in want:
             extras["tangents_normals"] = bench_derivs(dev, xs, args.warmup, flush, peak, plan, kn, ct, pr, npts,
                                                       pk.descs)
@@ -336,7 +336,8 @@ def _time_steps(fn, steps, warmup, flush, stream):
 
 def bench_curves(dev, steps, warmup, flush, peak):
     """4096 cubic 3-D curves, 64 control points, 1024 samples: one fused fit step
-    (forward, MSE, backward, Adam on control points and weights) per call."""
+    (forward, MSE, backward, Adam on control points and weights) per call, and the
+    forward alone (points written, 12 B per sample)."""
     import torch
     from paper_2104_14547_gb300 import batch, synth, tune
     curves, targets = synth.cubic_curve_batch(0, 4096, 64, 1024)
@@ -360,10 +361,19 @@ def bench_curves(dev, steps, warmup, flush, peak):
     nctrl = int(pk.descs["n1"].sum())
     abytes = 12 * pk.npts + nctrl * (16 * 2 + 32 * 2) + 4 * (len(pk.knots) + len(pk.params)) + 4 * pk.count
     ach = abytes / (ms / 1e3) / 1e9
-    return {"workload": "4096 cubic 3-D curves, 64 control points, 1024 samples, fused fit step (fwd + MSE + bwd + Adam)",
-            "value": pk.npts / (ms / 1e3), "unit": "curve pts/s", "ms_per_step": ms,
-            "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                         "algorithmic_bytes": abytes}}
+    fit = {"workload": "4096 cubic 3-D curves, 64 control points, 1024 samples, fused fit step (fwd + MSE + bwd + Adam)",
+           "value": pk.npts / (ms / 1e3), "unit": "curve pts/s", "ms_per_step": ms,
+           "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                        "algorithmic_bytes": abytes}}
+    pts = torch.empty((pk.npts, 3), device=dev)
+    ms = _time_steps(lambda: plan.eval(kn, ct, pr, pts), steps, warmup, flush, stream)
+    abytes = 12 * pk.npts + 16 * nctrl + 4 * (len(pk.knots) + len(pk.params))
+    ach = abytes / (ms / 1e3) / 1e9
+    ev = {"workload": "the same curves, forward only (points written)",
+          "value": pk.npts / (ms / 1e3), "unit": "curve pts/s", "ms_per_step": ms,
+          "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                       "algorithmic_bytes": abytes}}
+    return fit, ev
 
 
 def bench_derivs(dev, steps, warmup, flush, peak, plan, kn, ct, pr, npts, descs):

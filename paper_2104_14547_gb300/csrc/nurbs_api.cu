@@ -58,6 +58,7 @@ struct nurbs_plan {
     int smem_bytes;           // gradient kernels
     int smem_eval;            // forward kernels (no shared adjoint)
     int c_mc, c_wbytes, c_smem;   // curve kernels: control capacity, bytes per warp, per CTA
+    int c_wbytes_f, c_smem_f;     // the same for the forward-only curve kernels
     float knot_sigma;             // smoothed-indicator knot derivative bandwidth (0: off)
     int grad_homog;               // control-point gradients with respect to Pw
     // workspace layout (bytes)
@@ -152,6 +153,7 @@ nurbs_status nurbs_plan_create(int32_t kind, const nurbs_desc* h_desc, int32_t c
     // one tile (one warp) per curve, one group per degree
     pl->c_mc = 4;
     pl->c_wbytes = 0;
+    pl->c_wbytes_f = 0;
     for (ItemDev& it : pl->items) {
         it.ck = (kind == NURBS_KIND_CURVE && it.m1 <= kCurveCtrlCap) ? 1 : 0;
         if (it.ck) pl->c_mc = std::max(pl->c_mc, it.m1);
@@ -176,10 +178,12 @@ nurbs_status nurbs_plan_create(int32_t kind, const nurbs_desc* h_desc, int32_t c
         grp.t1 = (int)pl->tiles.size();
         if (grp.t1 > grp.t0) {
             pl->groups.push_back(grp);
-            pl->c_wbytes = std::max(pl->c_wbytes, curve_warp_bytes(pl->c_mc, q));
+            pl->c_wbytes = std::max(pl->c_wbytes, curve_warp_bytes(pl->c_mc, q, true));
+            pl->c_wbytes_f = std::max(pl->c_wbytes_f, curve_warp_bytes(pl->c_mc, q, false));
         }
     }
     pl->c_smem = kCurveWarps * pl->c_wbytes;
+    pl->c_smem_f = kCurveWarps * pl->c_wbytes_f;
     // tiles, grouped by degree pair so that each group runs one specialised kernel
     for (int g = 0; g < kMaxGroups; ++g) {
         const int gp = g / 5, gq = g % 5 + 1;
@@ -380,7 +384,8 @@ struct GroupLaunch {
 GroupLaunch group_launch(const nurbs_plan* pl, const PlanGroup& grp, int v)
 {
     if (grp.ck)
-        return GroupLaunch{curve_variant(v, grp.q), 32 * kCurveWarps, pl->c_smem, kMaxGroups + grp.q - 1, kCurveWarps};
+        return GroupLaunch{curve_variant(v, grp.q), 32 * kCurveWarps, (v == 0 || v == 5) ? pl->c_smem_f : pl->c_smem,
+                           kMaxGroups + grp.q - 1, kCurveWarps};
     return GroupLaunch{variant_for(v, grp.p, grp.q), 32 * pl->warps, (v == 0 || v == 5) ? pl->smem_eval : pl->smem_bytes,
                        grp.p * 5 + grp.q - 1, 1};
 }
@@ -439,6 +444,7 @@ void fill_tables(KParams& kp, const nurbs_plan* pl, unsigned char* ws)
 nurbs_status launch_groups(nurbs_plan* pl, int v, KParams& kp, unsigned char* ws, cudaStream_t s, bool cap)
 {
     fill_tables(kp, pl, ws);
+    kp.c_wbytes = (v == 0 || v == 5) ? pl->c_wbytes_f : pl->c_wbytes;   // curve kernels' bytes per warp
     for (PlanGroup& grp : pl->groups) {
         const GroupLaunch gl = group_launch(pl, grp, v);
         nurbs_status st = size_group(pl, grp, v, gl, cap);

@@ -2,8 +2,10 @@
 //
 // A curve C(u) = sum_r N_r(u) Pw_r / W (the curve form of Eq. 3) has no second
 // direction to share work across, so the tile kernels' row/column split does
-// not fit it.  Here lane L of a warp takes the contiguous samples
-// [L*nb, (L+1)*nb) of its curve.  Samples are non-decreasing, so the lane walks
+// not fit it.  The forward alone interleaves the samples over the lanes
+// (curve_eval_body).  The gradient kernels accumulate the adjoint of the net
+// instead: lane L of a warp takes the contiguous samples [L*nb, (L+1)*nb) of
+// its curve.  Samples are non-decreasing, so the lane walks
 // them with the knot span never decreasing and keeps in registers:
 //   - the window of the P+1 homogeneous control points Pw[s-P .. s];
 //   - their adjoint accumulators tau[r] = sum_b N_r(u_b) lambda_b, where
@@ -45,19 +47,29 @@ constexpr int kCurveCtrlCap = 256;    // control points per curve on this path (
 //                        chunks of 4 targets (x y z); lane L's chunk c sits at slot
 //                        c ^ ((L >> 1) & 3) so that the lanes' 128-bit reads of one
 //                        chunk hit 8 distinct bank groups per quarter warp
+// The forward-only kernels (curve_eval_body) keep just the knots [0, 4 kc) and the
+// net as homogeneous points (16 mc).
 __host__ __device__ constexpr int curve_kc(int mc, int P) { return (mc + P + 1 + 3) & ~3; }
-__host__ __device__ constexpr int curve_off_aov(int mc, int P) { return 8 * curve_kc(mc, P) + 16 * mc + 512; }
+__host__ __device__ constexpr int curve_off_lanes(int mc, int P) { return 8 * curve_kc(mc, P) + 16 * mc; }
+__host__ __device__ constexpr int curve_off_aov(int mc, int P) { return curve_off_lanes(mc, P) + 512; }
 __host__ __device__ constexpr int curve_off_net(int mc, int P)
 {
     return (curve_off_aov(mc, P) + 512 * (P + 1) + 256 * P + 15) & ~15;
 }
 __host__ __device__ constexpr int curve_off_ring(int mc, int P) { return curve_off_net(mc, P) + 16 * mc; }
-__host__ __device__ constexpr int curve_warp_bytes(int mc, int P)
+__host__ __device__ constexpr int curve_warp_bytes(int mc, int P, bool grad)
 {
-    return curve_off_ring(mc, P) + kCurveStages * 32 * 16 * 4;
+    return grad ? curve_off_ring(mc, P) + kCurveStages * 32 * 16 * 4 : 4 * curve_kc(mc, P) + 16 * mc;
 }
 
-template <int P, bool GRAD, bool KNOTS, bool MSE, bool DER = false>
+// 16 bytes from shared to global memory (both 16-byte aligned)
+__device__ __forceinline__ void st_global16(float* dst, const float* src)
+{
+    *reinterpret_cast<float4*>(dst) = *reinterpret_cast<const float4*>(src);
+}
+
+// Gradient kernels (backward, MSE, fit step): the per-lane window walk above.
+template <int P, bool KNOTS, bool MSE>
 __device__ __forceinline__ void curve_body(const KParams& kp, int t, unsigned char* wsm)
 {
     constexpr int PB = P + 1;
@@ -69,7 +81,7 @@ __device__ __forceinline__ void curve_body(const KParams& kp, int t, unsigned ch
     float* s_kn = reinterpret_cast<float*>(wsm);
     float4* s_A = reinterpret_cast<float4*>(wsm + 4 * kc);
     float* s_K = reinterpret_cast<float*>(wsm + 4 * kc + 16 * mc);
-    int* s_ln = reinterpret_cast<int*>(wsm + 8 * kc + 16 * mc);
+    int* s_ln = reinterpret_cast<int*>(wsm + curve_off_lanes(mc, P));
     float4* s_Aov = reinterpret_cast<float4*>(wsm + curve_off_aov(mc, P));
     float* s_Kov = reinterpret_cast<float*>(wsm + curve_off_aov(mc, P) + 512 * PB);
     float4* s_net = reinterpret_cast<float4*>(wsm + curve_off_net(mc, P));
@@ -81,7 +93,7 @@ __device__ __forceinline__ void curve_body(const KParams& kp, int t, unsigned ch
     const float* __restrict__ gU = kp.knots + it.knot_v;
     const float* __restrict__ gu = kp.params + it.param_v;
     const float4* __restrict__ gP = kp.ctrl + it.ctrl;
-    const float* __restrict__ gt = GRAD ? kp.gin + 3 * it.pts : nullptr;
+    const float* __restrict__ gt = kp.gin + 3 * it.pts;
 
     for (int k = lane; k < nk; k += 32) cp_async4(s_kn + k, gU + k);
     for (int i = lane; i < nc; i += 32)
@@ -94,7 +106,7 @@ __device__ __forceinline__ void curve_body(const KParams& kp, int t, unsigned ch
     const bool act = b0 < b1;
     const int rounds = nb / R;
     const int nact = nb > 0 ? (ns + nb - 1) / nb : 0;   // active lanes form a prefix
-    const bool al16 = ((it.param_v & 3) == 0) && (!GRAD || (it.pts & 3) == 0);
+    const bool al16 = ((it.param_v & 3) == 0) && ((it.pts & 3) == 0);
     const int swz = (lane >> 1) & 3;
     auto issue = [&](int k) {
         if (k < rounds) {
@@ -102,22 +114,18 @@ __device__ __forceinline__ void curve_body(const KParams& kp, int t, unsigned ch
             float* dst = s_ring + ((k & (kCurveStages - 1)) * 32 + lane) * 16;
             if (al16 && bb + R <= b1) {
                 cp_async16(dst + 4 * (0 ^ swz), gu + bb);
-                if constexpr (GRAD) {
-                    cp_async16(dst + 4 * (1 ^ swz), gt + 3 * bb);
-                    cp_async16(dst + 4 * (2 ^ swz), gt + 3 * bb + 4);
-                    cp_async16(dst + 4 * (3 ^ swz), gt + 3 * bb + 8);
-                }
+                cp_async16(dst + 4 * (1 ^ swz), gt + 3 * bb);
+                cp_async16(dst + 4 * (2 ^ swz), gt + 3 * bb + 4);
+                cp_async16(dst + 4 * (3 ^ swz), gt + 3 * bb + 8);
             } else {
 #pragma unroll
                 for (int j = 0; j < R; ++j) {
                     if (bb + j < b1) {
                         cp_async4(dst + 4 * (0 ^ swz) + j, gu + bb + j);
-                        if constexpr (GRAD) {
 #pragma unroll
-                            for (int c = 0; c < 3; ++c) {
-                                const int w = 3 * j + c;   // target word of the round
-                                cp_async4(dst + 4 * ((1 + w / 4) ^ swz) + (w & 3), gt + 3 * (bb + j) + c);
-                            }
+                        for (int c = 0; c < 3; ++c) {
+                            const int w = 3 * j + c;   // target word of the round
+                            cp_async4(dst + 4 * ((1 + w / 4) ^ swz) + (w & 3), gt + 3 * (bb + j) + c);
                         }
                     }
                 }
@@ -128,6 +136,8 @@ __device__ __forceinline__ void curve_body(const KParams& kp, int t, unsigned ch
 #pragma unroll
     for (int k = 0; k < kCurveStages; ++k) issue(k);
     cp_async_wait<kCurveStages>();   // the knots and the control net
+    __syncwarp();
+    for (int i = lane; i < nc; i += 32) s_net[i] = homog(s_net[i]);   // kept as Pw from here on
     __syncwarp();
 
     // device checks and the spans of this lane's first and last samples
@@ -170,16 +180,14 @@ __device__ __forceinline__ void curve_body(const KParams& kp, int t, unsigned ch
     // the window starts at the span of the lane's first sample
     if (act) {
 #pragma unroll
-        for (int r = 0; r < PB; ++r) Qw[r] = homog(s_net[sf - P + r]);
+        for (int r = 0; r < PB; ++r) Qw[r] = s_net[sf - P + r];
         cur = sf;
     }
     // move the window to span s (s >= cur): retire what leaves, load what enters
     auto advance = [&](int s) {
         while (cur < s) {
-            if constexpr (GRAD) {
-                retire_row(cur - P, tau[0]);
-                if constexpr (KNOTS) retire_knot(cur - P + 1, kacc[0]);
-            }
+            retire_row(cur - P, tau[0]);
+            if constexpr (KNOTS) retire_knot(cur - P + 1, kacc[0]);
 #pragma unroll
             for (int r = 0; r < P; ++r) { Qw[r] = Qw[r + 1]; tau[r] = tau[r + 1]; }
             tau[P] = f4zero();
@@ -189,13 +197,22 @@ __device__ __forceinline__ void curve_body(const KParams& kp, int t, unsigned ch
                 kacc[KW - 1] = 0.f;
             }
             ++cur;
-            if (cur > s - PB) Qw[P] = homog(s_net[cur]);   // only the last P+1 matter
+            if (cur > s - PB) Qw[P] = s_net[cur];   // only the last P+1 matter
         }
     };
 
     const bool has_pts = kp.pts != nullptr;
+    // Points of a round take the place of its targets in the ring and leave in three
+    // 16-byte stores per lane: scattered 4-byte stores, 384 bytes apart across the
+    // warp, cost several times more than the point's arithmetic.  The knot-gradient
+    // kernels have no registers to spare for it and store points directly.
+    constexpr bool kStage = !KNOTS;
+    // this lane's chunk offsets in a ring stage (floats); word w = 3j + c of a round's
+    // targets (and points) sits in chunk 1 + w / 4
+    const int o0 = 4 * (0 ^ swz), o1 = 4 * (1 ^ swz), o2 = 4 * (2 ^ swz), o3 = 4 * (3 ^ swz);
+    auto word = [&](int w) { return ((w < 4) ? o1 : (w < 8) ? o2 : o3) + (w & 3); };
     // one sample: span, basis, point, MSE and the adjoint accumulations
-    auto process = [&](int b, float u, float gx, float gy, float gz) {
+    auto process = [&](int b, float u, float gx, float gy, float gz, float* rb, int j) {
         if (!(u >= ulo && u <= uhi)) err |= kErrDomain;
         if (u < uprev) err |= kErrOrder;
         uprev = u;
@@ -211,95 +228,82 @@ __device__ __forceinline__ void curve_body(const KParams& kp, int t, unsigned ch
         if (s < n && !(u < s_kn[s + 1])) s = find_span(n, P, u, s_kn);
         advance(s);
         float N[PB];
-        float dN[DER ? PB : 1];
-        if constexpr (DER) basis_funs_d<P>(s, u, s_kn, N, dN);
-        else basis_funs<P>(s, u, s_kn, N);
+        basis_funs<P>(s, u, s_kn, N);
         float4 Cw = f4zero();
 #pragma unroll
         for (int r = 0; r < PB; ++r) Cw = fma4(N[r], Qw[r], Cw);
         const float inv = rcp_approx(Cw.w);
         const float Sx = Cw.x * inv, Sy = Cw.y * inv, Sz = Cw.z * inv;
         if (has_pts) {
-            float* o = kp.pts + 3 * (it.pts + b);
-            o[0] = Sx; o[1] = Sy; o[2] = Sz;
-        }
-        if constexpr (DER) {
-            // tangent C' = (A' - W' C) / W with (A', W') = sum_r dN_r Pw_r
-            if (kp.d_dv != nullptr) {
-                float4 Cd = f4zero();
-#pragma unroll
-                for (int r = 0; r < PB; ++r) Cd = fma4(dN[r], Qw[r], Cd);
-                float* o = kp.d_dv + 3 * (it.pts + b);
-                o[0] = (Cd.x - Cd.w * Sx) * inv;
-                o[1] = (Cd.y - Cd.w * Sy) * inv;
-                o[2] = (Cd.z - Cd.w * Sz) * inv;
+            if constexpr (kStage) {
+                rb[word(3 * j)] = Sx; rb[word(3 * j + 1)] = Sy; rb[word(3 * j + 2)] = Sz;
+            } else {
+                float* o = kp.pts + 3 * (it.pts + b);
+                o[0] = Sx; o[1] = Sy; o[2] = Sz;
             }
         }
-        if constexpr (GRAD) {
-            float ginv = inv;
-            if constexpr (MSE) {
-                gx = Sx - gx; gy = Sy - gy; gz = Sz - gz;
-                lossacc = fmaf(gx, gx, fmaf(gy, gy, fmaf(gz, gz, lossacc)));
-                ginv *= kp.grad_scale;
-            }
-            const float lx = gx * ginv, ly = gy * ginv, lz = gz * ginv;
-            const float4 lam = make_float4(lx, ly, lz, -fmaf(Sx, lx, fmaf(Sy, ly, Sz * lz)));
+        float ginv = inv;
+        if constexpr (MSE) {
+            gx = Sx - gx; gy = Sy - gy; gz = Sz - gz;
+            lossacc = fmaf(gx, gx, fmaf(gy, gy, fmaf(gz, gz, lossacc)));
+            ginv *= kp.grad_scale;
+        }
+        const float lx = gx * ginv, ly = gy * ginv, lz = gz * ginv;
+        const float4 lam = make_float4(lx, ly, lz, -fmaf(Sx, lx, fmaf(Sy, ly, Sz * lz)));
 #pragma unroll
-            for (int r = 0; r < PB; ++r) tau[r] = fma4(N[r], lam, tau[r]);
-            if constexpr (KNOTS) {
-                float beta[PB];
+        for (int r = 0; r < PB; ++r) tau[r] = fma4(N[r], lam, tau[r]);
+        if constexpr (KNOTS) {
+            float beta[PB];
 #pragma unroll
-                for (int r = 0; r < PB; ++r) beta[r] = dot4(Qw[r], lam);
-                float dk[2 * P + 1];
-                basis_knot_vjp<P>(s, u, s_kn, beta, dk);
-                if (kp.knot_sigma > 0.f) knot_sigma_terms<P>(s, u, s_kn, beta, kp.knot_sigma, dk);
+            for (int r = 0; r < PB; ++r) beta[r] = dot4(Qw[r], lam);
+            float dk[2 * P + 1];
+            basis_knot_vjp<P>(s, u, s_kn, beta, dk);
+            if (kp.knot_sigma > 0.f) knot_sigma_terms<P>(s, u, s_kn, beta, kp.knot_sigma, dk);
 #pragma unroll
-                for (int q = 0; q < KW; ++q) kacc[q] += dk[q];
-            }
+            for (int q = 0; q < KW; ++q) kacc[q] += dk[q];
         }
     };
 
-    // this lane's chunk offsets in a ring stage (floats)
-    const int o0 = 4 * (0 ^ swz), o1 = 4 * (1 ^ swz), o2 = 4 * (2 ^ swz), o3 = 4 * (3 ^ swz);
+    const bool st16 = has_pts && (it.pts & 3) == 0;
     for (int k = 0; k < rounds; ++k) {
         cp_async_wait<kCurveStages - 1>();   // round k has landed (later ones may be in flight)
-        const float* rb = s_ring + ((k & (kCurveStages - 1)) * 32 + lane) * 16;
+        float* rb = s_ring + ((k & (kCurveStages - 1)) * 32 + lane) * 16;
         const int bb = b0 + k * R;
-        // target word w = 3j + c of the round sits in chunk 1 + w / 4
         // one copy of the per-sample body (unrolling it four times costs more in
         // instruction fetch than it saves)
 #pragma unroll 1
         for (int j = 0; j < R; ++j) {
             if (bb + j < b1) {
-                float g[3] = {0.f, 0.f, 0.f};
-                if constexpr (GRAD) {
+                float g[3];
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        const int w = 3 * j + c;
-                        const int oc = (w < 4) ? o1 : (w < 8) ? o2 : o3;
-                        g[c] = rb[oc + (w & 3)];
-                    }
-                }
-                process(bb + j, rb[o0 + j], g[0], g[1], g[2]);
+                for (int c = 0; c < 3; ++c) g[c] = rb[word(3 * j + c)];
+                process(bb + j, rb[o0 + j], g[0], g[1], g[2], rb, j);
+            }
+        }
+        if (kStage && has_pts) {   // sample j's targets were read before its point was written
+            float* o = kp.pts + 3 * (it.pts + (long long)bb);
+            if (st16 && bb + R <= b1) {
+                st_global16(o, rb + o1);
+                st_global16(o + 4, rb + o2);
+                st_global16(o + 8, rb + o3);
+            } else {
+                for (int w = 0; w < 3 * min(R, b1 - bb); ++w) o[w] = rb[word(w)];
             }
         }
         __syncwarp();
         issue(k + kCurveStages);   // the stage just read is refilled for a later round
     }
-    if constexpr (GRAD) {
-        if (cur >= 0) {
+    if (cur >= 0) {
 #pragma unroll
-            for (int r = 0; r < PB; ++r) retire_row(cur - P + r, tau[r]);
-            if constexpr (KNOTS) {
+        for (int r = 0; r < PB; ++r) retire_row(cur - P + r, tau[r]);
+        if constexpr (KNOTS) {
 #pragma unroll
-                for (int q = 0; q < KW; ++q) retire_knot(cur - P + 1 + q, kacc[q]);
-            }
+            for (int q = 0; q < KW; ++q) retire_knot(cur - P + 1 + q, kacc[q]);
         }
     }
     cp_async_wait<0>();
     if (err) atomicOr(&kp.hdr->error, err);
     __syncwarp();
-    if constexpr (!GRAD) return;
 
 #pragma unroll
     for (int o = 16; o >= 1; o >>= 1) lossacc += __shfl_xor_sync(0xffffffffu, lossacc, o);
@@ -327,7 +331,7 @@ __device__ __forceinline__ void curve_body(const KParams& kp, int t, unsigned ch
                 const int i = i0 + 32 * e;
                 a[e] = c[e] = mm[e] = vv[e] = f4zero();
                 if (i >= nc) continue;
-                c[e] = s_net[i];
+                c[e] = kp.ctrl[it.ctrl + i];
                 if (kp.fit) { mm[e] = kp.adam_m[it.ctrl + i]; vv[e] = kp.adam_v[it.ctrl + i]; }
                 bool first = true;
                 for (int l = first_lane(i); l < nact && s_ln[l] - P <= i; ++l) {
@@ -373,8 +377,112 @@ __device__ __forceinline__ void curve_body(const KParams& kp, int t, unsigned ch
     __syncwarp();
 }
 
+// Forward (points, and tangents when DER): no adjoint to accumulate, so no
+// window walk.  Lane L takes samples L, L + 32, ... of the curve: the warp's 32
+// samples are consecutive, the stores of a step are contiguous and no lane has a
+// span change of its own for the warp to wait on.  The spans of one step are
+// non-decreasing across the lanes and not below the previous step's last span
+// s0, so the warp stages the 32 knots U[s0+1 .. s0+32] one per lane and each lane
+// counts those <= u by a shuffle binary search (the largest k with U_k <= u, as
+// find_span).  A lane whose u lies past all 32 (fewer samples than spans) falls
+// back to the binary search over the whole knot vector.
+template <int P, bool DER>
+__device__ __forceinline__ void curve_eval_body(const KParams& kp, int t, unsigned char* wsm)
+{
+    constexpr int PB = P + 1;
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int kc = curve_kc(kp.c_mc, P);
+    float* s_kn = reinterpret_cast<float*>(wsm);
+    float4* s_net = reinterpret_cast<float4*>(wsm + 4 * kc);   // homogeneous Pw
+
+    const int item = kp.tiles[t].item;
+    const ItemDev it = kp.items[item];
+    const int nc = it.m1, n = nc - 1, ns = it.nv, nk = nc + P + 1;
+    const float* __restrict__ gU = kp.knots + it.knot_v;
+    const float* __restrict__ gu = kp.params + it.param_v;
+    const float4* __restrict__ gP = kp.ctrl + it.ctrl;
+    for (int k = lane; k < nk; k += 32) s_kn[k] = __ldg(gU + k);
+    for (int i = lane; i < nc; i += 32) s_net[i] = homog(__ldg(gP + i));
+    __syncwarp();
+
+    unsigned err = 0;
+    for (int k = lane; k < nk - 1; k += 32)
+        if (s_kn[k] > s_kn[k + 1]) err |= kErrKnots;
+    if (lane == 0 && !(s_kn[n] < s_kn[n + 1])) err |= kErrKnots;
+    const float ulo = s_kn[P], uhi = s_kn[n + 1];
+    float* __restrict__ pts = kp.pts != nullptr ? kp.pts + 3 * it.pts : nullptr;
+    float* __restrict__ tan = DER && kp.d_dv != nullptr ? kp.d_dv + 3 * it.pts : nullptr;
+
+    int s0 = P;               // last span of the previous step
+    float ulast = -3.0e38f;   // last sample of the previous step
+    // parameters two steps ahead are in flight while a step computes (lanes past the
+    // end take the last knot)
+    auto load_u = [&](int b) { return b < ns ? __ldg(gu + b) : uhi; };
+    float u1 = load_u(lane), u2 = load_u(32 + lane);
+    for (int b0 = 0; b0 < ns; b0 += 32) {
+        const int b = b0 + lane;
+        const bool act = b < ns;
+        float u = u1;
+        u1 = u2;
+        u2 = load_u(b0 + 64 + lane);
+        if (act && !(u >= ulo && u <= uhi)) err |= kErrDomain;
+        const float up = __shfl_up_sync(full, u, 1);
+        if (act && u < (lane == 0 ? ulast : up)) err |= kErrOrder;
+        ulast = __shfl_sync(full, u, 31);
+        u = fminf(fmaxf(u, ulo), uhi);
+        // count the staged knots U[s0+1 .. s0+32] (only those up to U[n]) that are <= u
+        const int kk = s0 + 1 + lane;
+        const float kv = kk <= n ? s_kn[kk] : 3.0e38f;
+        int cnt = 0;
+#pragma unroll
+        for (int step = 16; step >= 1; step >>= 1) {
+            const float k = __shfl_sync(full, kv, cnt + step - 1);
+            if (k <= u) cnt += step;
+        }
+        const float kv31 = __shfl_sync(full, kv, 31);   // every lane takes part in each shuffle
+        int s = min(s0 + cnt, n);   // (the bound matters only for non-finite knots)
+        if (cnt == 31 && kv31 <= u) s = find_span(n, P, u, s_kn);
+        s0 = __shfl_sync(full, s, 31);
+        if (!act) continue;
+        float N[PB];
+        float dN[DER ? PB : 1];
+        if constexpr (DER) basis_funs_d<P>(s, u, s_kn, N, dN);
+        else basis_funs<P>(s, u, s_kn, N);
+        float4 Cw = f4zero(), Cd = f4zero();
+#pragma unroll
+        for (int r = 0; r < PB; ++r) {
+            const float4 pw = s_net[s - P + r];
+            Cw = fma4(N[r], pw, Cw);
+            if constexpr (DER) Cd = fma4(dN[r], pw, Cd);
+        }
+        const float inv = rcp_approx(Cw.w);
+        const float Sx = Cw.x * inv, Sy = Cw.y * inv, Sz = Cw.z * inv;
+        if (pts != nullptr) {
+            float* o = pts + 3 * (long long)b;
+            o[0] = Sx; o[1] = Sy; o[2] = Sz;
+        }
+        if constexpr (DER) {
+            // tangent C' = (A' - W' C) / W with (A', W') = sum_r dN_r Pw_r
+            if (tan != nullptr) {
+                float* o = tan + 3 * (long long)b;
+                o[0] = (Cd.x - Cd.w * Sx) * inv;
+                o[1] = (Cd.y - Cd.w * Sy) * inv;
+                o[2] = (Cd.z - Cd.w * Sz) * inv;
+            }
+        }
+    }
+    if (err) atomicOr(&kp.hdr->error, err);
+    __syncwarp();
+}
+
+// Resident CTAs per SM: the gradient kernels need 128 registers a thread.
+template <int P, bool GRAD>
+constexpr int curve_min_blocks() { return GRAD ? 4 : 8; }
+
 template <int P, bool GRAD, bool KNOTS, bool MSE, bool DER = false>
-__global__ void __launch_bounds__(32 * kCurveWarps, 4) curves_kernel(const __grid_constant__ KParams kp)
+__global__ void __launch_bounds__(32 * kCurveWarps, curve_min_blocks<P, GRAD>())
+    curves_kernel(const __grid_constant__ KParams kp)
 {
     extern __shared__ float4 smem4[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -382,7 +490,8 @@ __global__ void __launch_bounds__(32 * kCurveWarps, 4) curves_kernel(const __gri
     // the first curve of each warp is its own index; later ones come from the queue
     int t = kp.t0 + (int)blockIdx.x * kCurveWarps + warp;
     while (t < kp.t1) {
-        curve_body<P, GRAD, KNOTS, MSE, DER>(kp, t, wsm);
+        if constexpr (GRAD) curve_body<P, KNOTS, MSE>(kp, t, wsm);
+        else curve_eval_body<P, DER>(kp, t, wsm);
         int nt = 0;
         if (lane == 0) nt = kp.t0 + (int)gridDim.x * kCurveWarps + (int)atomicAdd(kp.queue, 1u);
         t = __shfl_sync(0xffffffffu, nt, 0);
