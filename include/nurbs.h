@@ -117,6 +117,19 @@ int32_t nurbs_plan_tiles(const nurbs_plan* plan);
 int32_t nurbs_plan_ctas(const nurbs_plan* plan);
 
 /*
+ * nurbs_plan_occupancy -- resident CTAs per SM of the plan's kernels for launch
+ * kind `op` (the fewest over its degree groups) and the largest dynamic shared
+ * memory of one CTA, in bytes (smem_bytes may be NULL).  op: 0 forward,
+ * 1 backward, 2 backward with knot gradients, 3 MSE step, 4 MSE step with knot
+ * gradients (also the fit step), 5 forward with tangents.  Lets a caller that
+ * runs several plans side by side size their CTA caps (nurbs_tile_cfg.max_ctas)
+ * by what really fits on an SM.  Queries the current device.
+ * Errors: NURBS_ERR_ARG, NURBS_ERR_SIZE (a kernel cannot hold the plan's tile),
+ * NURBS_ERR_CUDA.
+ */
+nurbs_status nurbs_plan_occupancy(const nurbs_plan* plan, int32_t op, int32_t* ctas_per_sm, int32_t* smem_bytes);
+
+/*
  * nurbs_plan_bind -- attach a device workspace to the plan: uploads the item and
  * tile tables and zeroes the counters and the error word (async on `stream`; the
  * host tables are staged in plan-owned host memory that stays valid until the

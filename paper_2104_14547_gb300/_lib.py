@@ -104,6 +104,7 @@ SIGNATURES = {
     "nurbs_plan_points": (_i64, [_vp]),
     "nurbs_plan_tiles": (_i32, [_vp]),
     "nurbs_plan_ctas": (_i32, [_vp]),
+    "nurbs_plan_occupancy": (_i32, [_vp, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
     "nurbs_plan_set_knot_sigma": (_i32, [_vp, _f]),
     "nurbs_plan_set_grad_homogeneous": (_i32, [_vp, _i32]),
     "nurbs_plan_bind": (_i32, [_vp, _vp, _sz, _vp]),

@@ -133,6 +133,7 @@ class Plan:
         self.kind = kind
         self.descs = np.ascontiguousarray(descs, dtype=DESC_DTYPE)
         self.count = len(self.descs)
+        self.warps = warps if warps > 0 else 8     # the library's default
         cfg = _lib.TileCfg(rows, warps, ctas_per_sm, max_ctas)
         h = ctypes.c_void_p()
         dptr = self.descs.ctypes.data_as(ctypes.POINTER(_lib.Desc))
@@ -174,6 +175,16 @@ class Plan:
         """Knot derivative of later gradient calls: 0 = almost-everywhere form,
         > 0 = the Gaussian-smoothed indicator of bandwidth sigma."""
         _lib.check(self.lib.nurbs_plan_set_knot_sigma(self.handle, ctypes.c_float(sigma)), "nurbs_plan_set_knot_sigma")
+
+    def occupancy(self, op: str = "mse_knots"):
+        """(resident CTAs per SM, dynamic shared bytes per CTA) of this plan's
+        kernels for op in {"eval", "backward", "backward_knots", "mse", "mse_knots",
+        "derivs"} ("mse_knots" also covers the fit step)."""
+        code = {"eval": 0, "backward": 1, "backward_knots": 2, "mse": 3, "mse_knots": 4, "derivs": 5}[op]
+        occ, smem = ctypes.c_int32(0), ctypes.c_int32(0)
+        _lib.check(self.lib.nurbs_plan_occupancy(self.handle, code, ctypes.byref(occ), ctypes.byref(smem)),
+                   "nurbs_plan_occupancy")
+        return int(occ.value), int(smem.value)
 
     def set_grad_homogeneous(self, on: bool):
         """Control-point gradients of later calls: False = (dL/dP, dL/dw) (default),

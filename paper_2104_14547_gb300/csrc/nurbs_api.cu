@@ -57,6 +57,7 @@ struct nurbs_plan {
         off_jb, off_win, off_run, off_knots, off_w, off_acc, off_sa, off_dnu;
     int smem_bytes;           // gradient kernels
     int smem_eval;            // forward kernels (no shared adjoint)
+    int smem_der;             // forward with tangents (derivative tables where the adjoint would be)
     int c_mc, c_wbytes, c_smem;   // curve kernels: control capacity, bytes per warp, per CTA
     int c_wbytes_f, c_smem_f;     // the same for the forward-only curve kernels
     float knot_sigma;             // smoothed-indicator knot derivative bandwidth (0: off)
@@ -277,11 +278,14 @@ nurbs_status nurbs_plan_create(int32_t kind, const nurbs_desc* h_desc, int32_t c
         max_knots = std::max(max_knots, align4(it.n1 + it.p + 1) + it.m1 + it.q + 1);
     pl->off_knots = take(4 * max_knots);
     pl->off_w = take(4 * (kJbCap + maxC * sv));
-    pl->off_dnu = take(4 * maxR * su);   // row basis derivatives (forward with tangents)
     size_t sa_bytes = 0;
     for (const ItemDev& it : pl->items)
         if (it.smemA) sa_bytes = std::max(sa_bytes, smem_adjoint_bytes(it, pl->tiles[it.first_tile].nwr));
     pl->smem_eval = (int)off;     // the forward kernels stop here
+    // the row basis derivatives of the forward with tangents take the place of the
+    // shared adjoint, which only the gradient kernels use
+    pl->off_dnu = (int)off;
+    pl->smem_der = (int)align_up(off + 4 * (size_t)maxR * su, 16);
     pl->off_sa = take(sa_bytes);
     pl->off_acc = pl->off_su;     // the final reduction reuses the tile tables
     int max_units = 1;
@@ -386,7 +390,8 @@ GroupLaunch group_launch(const nurbs_plan* pl, const PlanGroup& grp, int v)
     if (grp.ck)
         return GroupLaunch{curve_variant(v, grp.q), 32 * kCurveWarps, (v == 0 || v == 5) ? pl->c_smem_f : pl->c_smem,
                            kMaxGroups + grp.q - 1, kCurveWarps};
-    return GroupLaunch{variant_for(v, grp.p, grp.q), 32 * pl->warps, (v == 0 || v == 5) ? pl->smem_eval : pl->smem_bytes,
+    return GroupLaunch{variant_for(v, grp.p, grp.q), 32 * pl->warps,
+                       v == 0 ? pl->smem_eval : v == 5 ? pl->smem_der : pl->smem_bytes,
                        grp.p * 5 + grp.q - 1, 1};
 }
 
@@ -481,6 +486,29 @@ int32_t nurbs_plan_ctas(const nurbs_plan* plan)
     int n = 0;
     for (const PlanGroup& g : plan->groups) n += *std::max_element(g.grid, g.grid + 6);
     return n;
+}
+
+nurbs_status nurbs_plan_occupancy(const nurbs_plan* plan, int32_t op, int32_t* ctas_per_sm, int32_t* smem_bytes)
+{
+    if (plan == nullptr || ctas_per_sm == nullptr || op < 0 || op > 5) return NURBS_ERR_ARG;
+    int occ_min = 0, smem_max = 0;
+    for (const PlanGroup& grp : plan->groups) {
+        const GroupLaunch gl = group_launch(plan, grp, op);
+        cudaError_t e = cudaSuccess;
+        if (gl.smem > 48 * 1024) {
+            int limit = 0;
+            e = gl.kv.set_smem(&limit);
+            if (e == cudaSuccess && gl.smem > limit) return NURBS_ERR_SIZE;
+        }
+        int occ = 0;
+        if (e == cudaSuccess) e = gl.kv.occupancy(&occ, gl.block, gl.smem);
+        if (e != cudaSuccess) return cuda_fail(e);
+        occ_min = occ_min == 0 ? occ : std::min(occ_min, occ);
+        smem_max = std::max(smem_max, gl.smem);
+    }
+    *ctas_per_sm = occ_min;
+    if (smem_bytes != nullptr) *smem_bytes = smem_max;
+    return NURBS_OK;
 }
 
 static nurbs_status eval_common(const nurbs_plan* pl, int32_t kind, const float* knots, const float* ctrl,

@@ -2,9 +2,12 @@
 
 A batch with mixed degrees, control nets and grids is packed once.  Items are
 grouped by degree pair; each group gets its own libnurbs plan over the shared
-packed arrays, a tile shape from the autotuner, and a CTA budget proportional to
-its share of the work, so the groups' persistent kernels run side by side on
-their own streams.  The whole step (forward + MSE + backward, or the fused fit
+packed arrays and a tile shape from the autotuner, and the groups' persistent
+kernels run side by side on their own streams.  By default no group's CTAs are
+capped: the hardware hands SM slots to whichever kernel has CTAs waiting, which
+measured faster on the 1000-surface batch (875 us) than splitting the SMs by
+work share (1221 us with a 16-warps-per-SM budget, 1801 us with the kernels'
+real occupancy).  The whole step (forward + MSE + backward, or the fused fit
 step) is captured into one CUDA graph and replayed.
 
 `per_item_step` runs the same kernels with one launch per surface: the
@@ -19,8 +22,15 @@ from . import _lib, batch, tune
 
 
 class RaggedEngine:
+    """tile: one (warps, rows) for every group instead of the per-group autotuner.
+    budget: how a group's CTA cap is sized -- "warps" (its work share of a wave of
+    16 warps per SM, what a 128-register tile kernel holds), "occupancy" (its
+    share of the CTAs its kernel really fits per SM, nurbs_plan_occupancy) or
+    "none" (no cap: the groups' persistent CTAs share the SMs first come, first
+    served)."""
+
     def __init__(self, surfaces, targets_pts: np.ndarray, device="cuda", autotune=True, knots_grad=True,
-                 candidates=None):
+                 candidates=None, tile=None, budget="none"):
         self.device = torch.device(device)
         if self.device.index is None:
             self.device = torch.device("cuda", torch.cuda.current_device())
@@ -36,6 +46,8 @@ class RaggedEngine:
         self.grad_scale = 2.0 / (3.0 * max(pk.npts, 1))
         self.points = pk.npts
         sms = torch.cuda.get_device_properties(self.device).multi_processor_count
+        op = "mse_knots" if knots_grad else "mse"
+        assert budget in ("warps", "occupancy", "none")
         # degree groups
         keys = sorted(set(zip(pk.descs["p"].tolist(), pk.descs["q"].tolist())))
         work = {k: 0 for k in keys}
@@ -46,21 +58,23 @@ class RaggedEngine:
         for k in keys:
             sel = np.nonzero((pk.descs["p"] == k[0]) & (pk.descs["q"] == k[1]))[0]
             sub = pk.descs[sel]
-            # CTA budget: this group's share of a full wave of CTA slots (a 128-register
-            # tile kernel fits 16 warps per SM), at least one SM's worth; tile shapes
-            # are tuned under that budget
+            # CTA budget: this group's share of a full wave of CTA slots, at least one
+            # SM's worth; tile shapes are tuned under that budget
             share = work[k] / total
 
-            def budget(w, share=share):
-                per_sm = max(1, 16 // w)
+            def cap(plan, share=share):
+                if budget == "none":
+                    return 0
+                per_sm = max(1, 16 // plan.warps) if budget == "warps" else max(1, plan.occupancy(op)[0])
                 return max(per_sm, int(round(share * sms * per_sm)))
 
-            warps, rows = 8, 128
-            if autotune:
+            warps, rows = tile if tile is not None else (8, 128)
+            if autotune and tile is None:
                 sub_packed = batch.Packed(pk.kind, sub, pk.knots, pk.ctrl, pk.params, pk.npts)
                 (warps, rows), _ = tune.autotune(sub_packed, self._tensors(), op="mse", candidates=candidates,
-                                                 reps=3, device=self.device, max_ctas=budget)
-            max_ctas = budget(warps)
+                                                 reps=3, device=self.device, max_ctas=cap,
+                                                 budget_key=(budget, round(share, 6), sms))
+            max_ctas = cap(batch.Plan(pk.kind, sub, device=self.device, warps=warps, rows=rows))
             plan = batch.Plan(pk.kind, sub, device=self.device, warps=warps, rows=rows, max_ctas=max_ctas)
             # loss_items is indexed by the plan's own item order: one buffer per group
             self.groups.append(dict(key=k, items=sel, plan=plan, tile=(warps, rows), max_ctas=max_ctas,

@@ -38,24 +38,31 @@ def _time(fn, reps, flush):
 
 
 def autotune(packed: batch.Packed, tensors: dict, op: str = "mse", candidates=None, reps: int = 5,
-             device="cuda", max_ctas=None):
+             device="cuda", max_ctas=None, budget_key=None):
     """Return (best (warps, rows), {cfg: ms}) for `op` in {"eval", "mse", "backward"}.
 
     tensors holds the device arrays the op needs: knots, ctrl, params and, for
     the gradient ops, target/grad_pts plus output buffers.  max_ctas, when
-    given, maps a warp count to the CTA cap each candidate is timed under (the
-    share of the GPU the plan will get when it runs beside others).
+    given, maps a candidate's plan (uncapped) to the CTA cap it is timed under
+    (the share of the GPU the plan will get when it runs beside others);
+    budget_key names that budget in the result cache.
     """
-    key = signature(packed, op) + ("" if max_ctas is None else repr([max_ctas(w) for w, _ in
-                                                                      (candidates or DEFAULT_CANDIDATES)]))
+    key = signature(packed, op) + repr(budget_key if max_ctas is not None else None)
     if key in _cache:
         return _cache[key]
     cands = candidates or DEFAULT_CANDIDATES
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=device)
     table = {}
     for warps, rows in cands:
-        cap = 0 if max_ctas is None else int(max_ctas(warps))
-        plan = batch.Plan.for_packed(packed, device=device, warps=warps, rows=rows, max_ctas=cap)
+        plan = batch.Plan.for_packed(packed, device=device, warps=warps, rows=rows)
+        if max_ctas is not None:
+            try:
+                cap = int(max_ctas(plan))
+            except _lib.NurbsError as e:
+                if e.status != _lib.ERR_SIZE:
+                    raise
+                continue
+            plan = batch.Plan.for_packed(packed, device=device, warps=warps, rows=rows, max_ctas=cap)
         kn, ct, pr = tensors["knots"], tensors["ctrl"], tensors["params"]
         if op == "eval":
             fn = lambda: plan.eval(kn, ct, pr, tensors["pts"])

@@ -120,3 +120,18 @@ def test_grad_homogeneous_setter_validates():
     assert lib.nurbs_plan_set_grad_homogeneous(h, -1) == 1
     assert lib.nurbs_plan_set_grad_homogeneous(None, 1) == 1
     lib.nurbs_plan_destroy(h)
+
+
+def test_occupancy_query_validates_arguments():
+    # argument errors are found before any device query
+    s = synth.single_bicubic(0)
+    pk = batch.pack_surfaces([s])
+    st, h = _plan(_lib.KIND_SURFACE, pk.descs)
+    assert st == 0
+    lib = _lib.load()
+    occ = ctypes.c_int32(0)
+    assert lib.nurbs_plan_occupancy(None, 4, ctypes.byref(occ), None) == 1
+    assert lib.nurbs_plan_occupancy(h, 6, ctypes.byref(occ), None) == 1
+    assert lib.nurbs_plan_occupancy(h, -1, ctypes.byref(occ), None) == 1
+    assert lib.nurbs_plan_occupancy(h, 4, None, None) == 1
+    lib.nurbs_plan_destroy(h)
