@@ -129,3 +129,44 @@ def test_streamed_steps_match_direct_step():
     assert torch.equal(host_out["grad_ctrl"], gc.cpu())
     assert torch.equal(host_out["grad_knots"], gk.cpu())
     assert torch.equal(host_out["loss"], loss.cpu())
+
+
+def test_engine_budgets_change_no_bits():
+    # CTA caps change only which SM runs a tile, never the result
+    surfs, T = _ragged(43, 24)
+    outs = []
+    for budget in ("none", "warps", "occupancy"):
+        eng = engine.RaggedEngine(surfs, T, tile=(4, 32), budget=budget)
+        assert len(eng.groups) > 1
+        eng.replay()
+        torch.cuda.synchronize()
+        assert all(e == 0 for e in eng.errors())
+        if budget != "none":
+            assert all(g["max_ctas"] > 0 for g in eng.groups)
+        outs.append((eng.pts.clone(), eng.grad_ctrl.clone(), eng.grad_knots.clone(), eng.item_losses()))
+    for o in outs[1:]:
+        for a, b in zip(outs[0][:3], o[:3]):
+            assert torch.equal(a, b)
+        assert np.array_equal(outs[0][3], o[3])
+
+
+def test_plan_occupancy_reports_what_launches():
+    surfs, _ = synth.bicubic_batch(0, 4, 32, 128)
+    pk = batch.pack_surfaces(surfs)
+    plan = batch.Plan.for_packed(pk, warps=8, rows=128)
+    occ, smem = plan.occupancy("mse_knots")
+    assert occ >= 1 and 48 * 1024 < smem <= 227 * 1024
+    occ_e, smem_e = plan.occupancy("eval")
+    assert smem_e < smem and occ_e >= occ          # the forward has no shared adjoint
+    assert plan.occupancy("derivs")[1] >= smem_e
+    # a plan as wide as the GPU holds: the grid of a long batch is occupancy x SMs
+    bpk = batch.pack_surfaces(synth.bicubic_batch(1, 1200, 8, 64)[0])
+    big = batch.Plan.for_packed(bpk, warps=8, rows=64)
+    kn, ct, pr = batch.to_device(bpk)
+    pts = torch.empty((big.points, 3), device="cuda")
+    big.eval(kn, ct, pr, pts)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    assert big.ctas == min(big.tiles, big.occupancy("eval")[0] * sms)
+    curves, _ = synth.cubic_curve_batch(0, 8, 64, 256)
+    cplan = batch.Plan.for_packed(batch.pack_curves(curves))
+    assert cplan.occupancy("eval")[0] == 8 and cplan.occupancy("mse")[0] == 4
