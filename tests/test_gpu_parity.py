@@ -63,6 +63,26 @@ def test_forward_curves():
     check_points(cs, CURVE, got)
 
 
+def test_curves_clustered_samples():
+    # samples in two clusters far apart in span: within one warp step some lanes are
+    # past the 32 staged knots of the forward's span search and take its fallback
+    # while the others do not; the gradient kernels' lanes jump many spans at once
+    rng = np.random.default_rng(44)
+    items = []
+    for p, n1 in ((3, 200), (2, 256), (5, 90)):
+        c = synth.curve(rng, p, n1, 2, knots="uniform")
+        u = np.concatenate([np.linspace(0.0, 0.02, 20), np.linspace(0.97, 1.0, 23),
+                            np.linspace(0.5, 0.5, 0)]).astype(np.float32)
+        items.append(synth.Curve(p, c.U, c.ctrl, np.sort(u)))
+        u2 = np.concatenate([np.linspace(0.0, 0.3, 7), np.linspace(0.31, 0.32, 70),
+                             np.linspace(0.6, 1.0, 9)]).astype(np.float32)
+        items.append(synth.Curve(p, c.U, c.ctrl, np.sort(u2)))
+    _, got = gpu_eval(items, CURVE)
+    check_points(items, CURVE, got)
+    pk, g, gc, gk = _run_backward(items, CURVE, 44)
+    _check_grads(items, CURVE, pk, g, gc, gk)
+
+
 def test_forward_edge_cases():
     rng = np.random.default_rng(4)
     # Bezier nets (n = p), samples exactly on uniform knots, a double interior knot,
