@@ -414,7 +414,7 @@ def bench_offset(dev, steps, warmup, flush, peak, count=4096):
     ach = abytes / (ms / 1e3) / 1e9
     return {"workload": f"{count} bicubic double-curved patches, 12x12 nets, 20x20 samples, offset d = {d}: "
                         "fused fit step toward the offset points",
-            "value": npts / (ms / 1e3), "unit": "surface pts/s", "ms_per_step": ms,
+            "value": npts / (ms / 1e3), "unit": "surface pts/s", "ms_per_step": ms, "tile": list(fit.tile),
             "max_deviation_over_d_after_300_steps": dev_fit / d,
             "control_point_offset_max_deviation_over_d": dev_cp / d,
             "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,

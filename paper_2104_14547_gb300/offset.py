@@ -15,11 +15,18 @@ from __future__ import annotations
 import numpy as np
 import torch
 
-from . import batch
+from . import batch, tune
+
+
+# small items (a few hundred samples) want narrow CTAs: one or two warps per item
+SMALL_ITEM_CANDIDATES = tune.DEFAULT_CANDIDATES + [(1, 32), (1, 64), (2, 64)]
 
 
 class OffsetFit:
-    def __init__(self, surfaces, distance, device="cuda", warps: int = 0, rows: int = 0):
+    """warps, rows: the fit step's tile shape; 0 and autotune=True let the tuner
+    pick it (fused MSE step timed on this batch)."""
+
+    def __init__(self, surfaces, distance, device="cuda", warps: int = 0, rows: int = 0, autotune: bool = True):
         self.device = torch.device(device)
         pk = batch.pack_surfaces(surfaces)
         self.packed = pk
@@ -40,6 +47,14 @@ class OffsetFit:
         self.adam_v = torch.zeros_like(base)
         self.loss = torch.zeros(pk.count, device=self.device)
         self.steps = 0
+        if autotune and warps == 0 and rows == 0:
+            scratch = dict(knots=self.knots, ctrl=base, params=self.params, target=self.target, pts=None,
+                           grad_ctrl=torch.empty_like(base), grad_knots=None, loss=self.loss)
+            (w, r), _ = tune.autotune(pk, scratch, op="mse", candidates=SMALL_ITEM_CANDIDATES, reps=3,
+                                      device=self.device)
+            self.plan = batch.Plan.for_packed(pk, device=self.device, warps=w, rows=r)
+            warps, rows = w, r
+        self.tile = (self.plan.warps, rows)       # rows 0: the planner's choice
 
     def step(self, lr: float = 2e-3):
         """One fused fit step (forward, MSE to the offset points, backward, Adam)."""
