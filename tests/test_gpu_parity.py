@@ -71,8 +71,7 @@ def test_curves_clustered_samples():
     items = []
     for p, n1 in ((3, 200), (2, 256), (5, 90)):
         c = synth.curve(rng, p, n1, 2, knots="uniform")
-        u = np.concatenate([np.linspace(0.0, 0.02, 20), np.linspace(0.97, 1.0, 23),
-                            np.linspace(0.5, 0.5, 0)]).astype(np.float32)
+        u = np.concatenate([np.linspace(0.0, 0.02, 20), np.linspace(0.97, 1.0, 23)]).astype(np.float32)
         items.append(synth.Curve(p, c.U, c.ctrl, np.sort(u)))
         u2 = np.concatenate([np.linspace(0.0, 0.3, 7), np.linspace(0.31, 0.32, 70),
                              np.linspace(0.6, 1.0, 9)]).astype(np.float32)
