@@ -305,6 +305,51 @@ def test_fit_step_surfaces_and_loss_decreases():
     assert hist[-1] < 0.5 * hist[0]
 
 
+def _fit_once_against_oracle(items, kind, lr=1e-2):
+    rng = np.random.default_rng(45)
+    pk = pack(items, kind)
+    T = rng.normal(size=(max(pk.npts, 1), 3)).astype(np.float32)
+    plan = batch.Plan.for_packed(pk)
+    kn, ct, pr = batch.to_device(pk)
+    m, v = torch.zeros_like(ct), torch.zeros_like(ct)
+    loss = torch.full((pk.count,), float("nan"), device="cuda")
+    before = batch.unpack_ctrl(pk, ct.cpu().numpy())
+    plan.fit_step(kn, ct, pr, torch.from_numpy(T).cuda(), m, v, 1, lr=lr, loss_items=loss)
+    assert plan.get_error()[0] == 0
+    after = batch.unpack_ctrl(pk, ct.cpu().numpy())
+    mm = batch.unpack_ctrl(pk, m.cpu().numpy())
+    lossn = loss.cpu().numpy()
+    for k, (it, Tk) in enumerate(zip(items, batch.unpack_points(pk, T))):
+        c0 = before[k].astype(np.float64)
+        npts = Tk.reshape(-1, 3).shape[0]
+        if npts == 0:                       # no samples: zero gradient, no move, zero loss
+            assert np.array_equal(after[k], before[k]) and np.all(mm[k] == 0) and lossn[k] == 0
+            continue
+        if kind == CURVE:
+            S = O.curve_eval(it.p, it.U, c0, it.u)
+            _, g = O.mse(S, Tk.astype(np.float64), 3 * pk.npts)
+            dc, _ = O.curve_vjp(it.p, it.U, c0, it.u, g, want_knots=False)
+        else:
+            S = O.surface_eval(it.p, it.q, it.U, it.V, c0, it.u, it.v)
+            _, g = O.mse(S, Tk.astype(np.float64), 3 * pk.npts)
+            dc, _, _ = O.surface_vjp(it.p, it.q, it.U, it.V, c0, it.u, it.v, g, want_knots=False)
+        th, _, _ = O.adam(c0, dc, np.zeros_like(dc), np.zeros_like(dc), 1, lr=lr)
+        sure = np.abs(dc) > 1e-2 * np.abs(dc).max()
+        assert np.abs(after[k] - th)[sure].max(initial=0.0) <= 1e-3 * lr + 1e-6 * np.abs(th).max(), k
+        assert abs(lossn[k] - float(((S - Tk) ** 2).sum())) <= 1e-4 * float(((S - Tk) ** 2).sum()) + 1e-6
+
+
+def test_fit_step_empty_and_single_sample_items():
+    rng = np.random.default_rng(46)
+    surfs = [synth.surface(rng, 3, 3, 8, 8, 20, 20), synth.surface(rng, 3, 3, 6, 6, 0, 10),
+             synth.surface(rng, 2, 3, 7, 6, 12, 0), synth.surface(rng, 3, 3, 9, 7, 1, 1),
+             synth.surface(rng, 3, 3, 10, 10, 33, 17)]
+    _fit_once_against_oracle(surfs, SURF)
+    curves = [synth.curve(rng, 3, 20, 200), synth.curve(rng, 3, 12, 0), synth.curve(rng, 2, 9, 1),
+              synth.curve(rng, 4, 300, 0, knots="uniform"), synth.curve(rng, 4, 300, 500, knots="uniform"), synth.curve(rng, 5, 64, 37)]
+    _fit_once_against_oracle(curves, CURVE)
+
+
 # ------------------------------------------------------------- device checks
 def test_device_checks_flag_bad_inputs():
     rng = np.random.default_rng(14)
