@@ -135,3 +135,34 @@ def test_occupancy_query_validates_arguments():
     assert lib.nurbs_plan_occupancy(h, -1, ctypes.byref(occ), None) == 1
     assert lib.nurbs_plan_occupancy(h, 4, None, None) == 1
     lib.nurbs_plan_destroy(h)
+
+
+@pytest.mark.parametrize("warps,rows", [(8, 0), (8, 128), (4, 32), (2, 7), (1, 0), (6, 50)])
+def test_planner_tile_count_follows_the_tiling_rule(warps, rows):
+    # a surface is cut into column tiles of at most 32 * warps samples (equal widths,
+    # rounded up to whole warps) and row tiles of `rows` samples (default: 16 rows per
+    # row group of warps); a curve on the curve kernels is one tile; longer curves are
+    # single-row surfaces
+    rng = np.random.default_rng(5)
+    shapes = [(40, 40), (1, 1), (0, 10), (10, 0), (129, 300), (513, 257), (64, 1000)]
+    surfs = [synth.surface(rng, 3, 2, 6, 7, nu, nv) for nu, nv in shapes]
+    pk = batch.pack_surfaces(surfs)
+    st, h = _plan(_lib.KIND_SURFACE, pk.descs, _lib.TileCfg(rows, warps, 0, 0))
+    assert st == 0
+    want = 0
+    for nu, nv in shapes:
+        nct = max(1, -(-nv // (32 * warps)))
+        width = -(-(-(-nv // nct)) // 32) * 32 if nv > 0 else 32
+        groups = max(1, warps // max(1, min(warps, width // 32)))
+        R = rows if rows > 0 else 16 * groups
+        want += max(1, -(-nu // R)) * nct
+    lib = _lib.load()
+    assert lib.nurbs_plan_tiles(h) == want
+    lib.nurbs_plan_destroy(h)
+    curves = [synth.curve(rng, 3, n1, ns, knots="uniform") for n1, ns in ((20, 100), (256, 7), (257, 700), (400, 0))]
+    ck = batch.pack_curves(curves)
+    st, h = _plan(_lib.KIND_CURVE, ck.descs, _lib.TileCfg(rows, warps, 0, 0))
+    assert st == 0
+    want = 2 + sum(max(1, -(-ns // (32 * warps))) for ns in (700, 0))
+    assert lib.nurbs_plan_tiles(h) == want
+    lib.nurbs_plan_destroy(h)
