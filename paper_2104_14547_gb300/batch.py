@@ -140,6 +140,7 @@ class Plan:
         _lib.check(self.lib.nurbs_plan_create(kind, dptr, self.count, ctypes.byref(cfg), ctypes.byref(h)),
                    "nurbs_plan_create")
         self.handle = h
+        self._extent = _extents(kind, self.descs)
         self.ws_bytes = int(self.lib.nurbs_plan_workspace_size(h))
         self.points = int(self.lib.nurbs_plan_points(h))
         self.tiles = int(self.lib.nurbs_plan_tiles(h))
@@ -166,7 +167,16 @@ class Plan:
         return int(self.lib.nurbs_plan_ctas(self.handle))
 
     # ---------------------------------------------------------------- calls
+    def _check(self, inputs=(), points=(), ctrl_like=(), knots_like=(), items=()):
+        check_tensors(self._extent, self.count, inputs, points, ctrl_like, knots_like, items)
+
+    def _inputs(self, knots, ctrl, params):
+        return [("knots", knots, "knots"), ("ctrl", ctrl, "ctrl"), ("params", params, "params")]
+
     def eval(self, knots, ctrl, params, pts, stream=None):
+        self._check(self._inputs(knots, ctrl, params), points=[("pts", pts)])
+        if pts is None:
+            raise ValueError("pts is required")
         fn = self.lib.nurbs_eval_curve if self.kind == _lib.KIND_CURVE else self.lib.nurbs_eval_surface
         _lib.check(fn(self.handle, _ptr(knots), _ptr(ctrl), _ptr(params), _ptr(pts), _stream(stream)), fn.__name__)
         return pts
@@ -195,6 +205,8 @@ class Plan:
     def eval_derivs(self, knots, ctrl, params, pts=None, du=None, dv=None, normals=None, stream=None):
         """Points with tangents and unit normals (surfaces: du, dv, normals; curves:
         the tangent goes to ``du``).  Outputs that are None are not written."""
+        self._check(self._inputs(knots, ctrl, params),
+                    points=[("pts", pts), ("du", du), ("dv", dv), ("normals", normals)])
         if self.kind == _lib.KIND_CURVE:
             _lib.check(self.lib.nurbs_eval_curve_derivs(self.handle, _ptr(knots), _ptr(ctrl), _ptr(params),
                                                         _ptr(pts), _ptr(du), _stream(stream)),
@@ -206,6 +218,8 @@ class Plan:
         return pts, du, dv, normals
 
     def backward(self, knots, ctrl, params, grad_pts, grad_ctrl=None, grad_knots=None, stream=None):
+        self._check(self._inputs(knots, ctrl, params) + [("grad_pts", grad_pts, "pts3")],
+                    ctrl_like=[("grad_ctrl", grad_ctrl)], knots_like=[("grad_knots", grad_knots)])
         _lib.check(self.lib.nurbs_backward(self.handle, _ptr(knots), _ptr(ctrl), _ptr(params), _ptr(grad_pts),
                                            _ptr(grad_ctrl), _ptr(grad_knots), _stream(stream)), "nurbs_backward")
 
@@ -213,6 +227,9 @@ class Plan:
                     loss_items=None, grad_scale=None, stream=None):
         if grad_scale is None:
             grad_scale = 2.0 / (3.0 * max(self.points, 1))
+        self._check(self._inputs(knots, ctrl, params) + [("target", target, "pts3")], points=[("pts", pts)],
+                    ctrl_like=[("grad_ctrl", grad_ctrl)], knots_like=[("grad_knots", grad_knots)],
+                    items=[("loss_items", loss_items)])
         _lib.check(self.lib.nurbs_mse_fwd_bwd(self.handle, _ptr(knots), _ptr(ctrl), _ptr(params), _ptr(target),
                                               _ptr(pts), _ptr(grad_ctrl), _ptr(grad_knots), _ptr(loss_items),
                                               ctypes.c_float(grad_scale), _stream(stream)), "nurbs_mse_fwd_bwd")
@@ -221,6 +238,9 @@ class Plan:
                  eps=1e-8, pts=None, loss_items=None, grad_knots=None, grad_scale=None, stream=None):
         if grad_scale is None:
             grad_scale = 2.0 / (3.0 * max(self.points, 1))
+        self._check(self._inputs(knots, ctrl, params) + [("target", target, "pts3"), ("adam_m", adam_m, "ctrl"),
+                                                          ("adam_v", adam_v, "ctrl")],
+                    points=[("pts", pts)], knots_like=[("grad_knots", grad_knots)], items=[("loss_items", loss_items)])
         hp = _lib.Adam(lr, betas[0], betas[1], eps)
         _lib.check(self.lib.nurbs_fit_step(self.handle, _ptr(knots), _ptr(ctrl), _ptr(params), _ptr(target),
                                            _ptr(pts), _ptr(adam_m), _ptr(adam_v), ctypes.byref(hp), int(step),
@@ -232,6 +252,46 @@ class Plan:
         flags = ctypes.c_uint32(0)
         st = self.lib.nurbs_plan_get_error(self.handle, _stream(stream), ctypes.byref(flags))
         return int(st), int(flags.value)
+
+
+def check_tensors(extent: dict, count: int, inputs=(), points=(), ctrl_like=(), knots_like=(), items=()):
+    """Refuse, on the host, tensors the kernels would index past.  inputs are
+    (name, tensor, kind) with kind one of the keys of `extent` (all required);
+    points, ctrl_like, knots_like and items are (name, tensor-or-None) sized like
+    the points (3 floats each), the control nets, the knot vectors and the items."""
+    need = [(n, t, extent[k], True) for n, t, k in inputs]
+    need += [(n, t, extent["pts3"], False) for n, t in points]
+    need += [(n, t, extent["ctrl"], False) for n, t in ctrl_like]
+    need += [(n, t, extent["knots"], False) for n, t in knots_like]
+    need += [(n, t, count, False) for n, t in items]
+    for name, t, n, required in need:
+        if t is None:
+            if required:
+                raise ValueError(f"{name} is required")
+            continue
+        if not isinstance(t, torch.Tensor) or t.dtype != torch.float32 or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous float32 tensor")
+        if t.numel() < n:
+            raise ValueError(f"{name} holds {t.numel()} floats; the plan's items need {n}")
+        if n > 0 and not t.is_cuda:
+            raise ValueError(f"{name} must be on the GPU")
+
+
+def _extents(kind: int, d: np.ndarray) -> dict:
+    """Floats each packed array must hold for the items of `d` (offsets + sizes)."""
+    i64 = lambda x: x.astype(np.int64)
+    top = lambda x: int(x.max(initial=0)) if len(x) else 0
+    if kind == _lib.KIND_CURVE:
+        knots = top(i64(d["knot_u"]) + d["n1"] + d["p"] + 1)
+        params = top(i64(d["param_u"]) + d["nu"])
+        ctrl = top(i64(d["ctrl"]) + d["n1"])
+        pts = top(i64(d["pts"]) + d["nu"])
+    else:
+        knots = max(top(i64(d["knot_u"]) + d["n1"] + d["p"] + 1), top(i64(d["knot_v"]) + d["m1"] + d["q"] + 1))
+        params = max(top(i64(d["param_u"]) + d["nu"]), top(i64(d["param_v"]) + d["nv"]))
+        ctrl = top(i64(d["ctrl"]) + i64(d["n1"]) * d["m1"])
+        pts = top(i64(d["pts"]) + i64(d["nu"]) * d["nv"])
+    return {"knots": knots, "params": params, "ctrl": 4 * ctrl, "pts": pts, "pts3": 3 * pts}
 
 
 def to_device(packed: Packed, device="cuda"):
