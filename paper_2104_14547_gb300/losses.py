@@ -23,9 +23,17 @@ def chamfer(P: torch.Tensor, p_sizes, Q: torch.Tensor, q_sizes, grad: bool = Tru
     with distances "dist_p", "dist_q".  bucketed=False takes the O(n m) gradient
     path (the same results, no scratch)."""
     dev = P.device
-    p_sizes = np.asarray(p_sizes, np.int64)
-    q_sizes = np.asarray(q_sizes, np.int64)
-    assert len(p_sizes) == len(q_sizes)
+    p_sizes = np.asarray(p_sizes, np.int64).reshape(-1)
+    q_sizes = np.asarray(q_sizes, np.int64).reshape(-1)
+    if len(p_sizes) != len(q_sizes):
+        raise ValueError("p_sizes and q_sizes must pair up")
+    if (p_sizes < 0).any() or (q_sizes < 0).any():
+        raise ValueError("set sizes must be non-negative")
+    for name, X, n in (("P", P, int(p_sizes.sum())), ("Q", Q, int(q_sizes.sum()))):
+        if X.numel() < 3 * n:                  # the kernels index every point of every pair
+            raise ValueError(f"{name} holds {X.numel()} floats; the sizes need {3 * n}")
+        if n > 0 and not X.is_cuda:
+            raise ValueError(f"{name} must be on the GPU")
     count = len(p_sizes)
     p_off = torch.from_numpy(np.concatenate([[0], np.cumsum(p_sizes)]).astype(np.int64)).to(dev)
     q_off = torch.from_numpy(np.concatenate([[0], np.cumsum(q_sizes)]).astype(np.int64)).to(dev)

@@ -44,3 +44,16 @@ def test_check_tensors_refuses_bad_arguments():
     # optional outputs may be absent, and zero-sized needs accept any tensor
     batch.check_tensors(ext, 2, points=[("pts", None)], ctrl_like=[("grad_ctrl", None)])
     batch.check_tensors({k: 0 for k in ext}, 0, inputs=[("knots", cpu, "knots")], items=[("loss", cpu)])
+
+
+def test_chamfer_refuses_bad_sizes_before_any_kernel():
+    from paper_2104_14547_gb300 import losses
+    P, Q = torch.zeros(10, 3), torch.zeros(8, 3)
+    with pytest.raises(ValueError, match="pair up"):
+        losses.chamfer(P, [5, 5], Q, [8])
+    with pytest.raises(ValueError, match="non-negative"):
+        losses.chamfer(P, [11, -1], Q, [4, 4])
+    with pytest.raises(ValueError, match="need 33"):
+        losses.chamfer(P, [5, 6], Q, [4, 4])
+    with pytest.raises(ValueError, match="GPU"):
+        losses.chamfer(P, [5, 5], Q, [4, 4])
