@@ -70,7 +70,11 @@ typedef struct nurbs_desc {
     int32_t n1, m1;      /* control points per direction (n+1, m+1) */
     int32_t nu, nv;      /* sample counts per direction */
     int32_t adam_step;   /* nurbs_fit_step: this item's 1-based Adam step (0 = the call's step) */
-    int32_t reserved1;
+    float grad_scale;    /* nurbs_mse_fwd_bwd / nurbs_fit_step / nurbs_mse_fwd_bwd_noalloc: this
+                            item's own scale of dL/dS = grad_scale * (S - T); 0 = the call's
+                            grad_scale.  2 / (3 nu nv) makes the item's loss the mean over its
+                            own points (Sec. 4, Eq. 12), so its gradient does not depend on the
+                            other items of the batch.  Negative or non-finite: NURBS_ERR_ARG. */
     int64_t knot_u;      /* offset of U in knots[] (floats) */
     int64_t knot_v;      /* offset of V in knots[] (floats) */
     int64_t ctrl;        /* offset of the control net in ctrl[] (float4 elements) */
@@ -241,8 +245,10 @@ nurbs_status nurbs_backward(const nurbs_plan* plan, const float* knots, const fl
  * squared error, Eq. 1 chain rule).
  *   pts         receives S, or NULL to skip the write
  *   loss_items  receives each item's sum of squared differences (float[count]), or NULL
- *   grad_scale  dL/dS = grad_scale * (S - T); 2 / (3 * total points) gives the
- *               gradient of the mean over all coordinates
+ *   grad_scale  dL/dS = grad_scale * (S - T) for items whose descriptor has
+ *               grad_scale == 0; 2 / (3 * total points) gives the gradient of the
+ *               mean over all coordinates of the batch.  An item with its own
+ *               descriptor grad_scale > 0 uses that instead (per-item mean loss).
  * grad_ctrl / grad_knots as in nurbs_backward (either may be NULL).
  */
 nurbs_status nurbs_mse_fwd_bwd(const nurbs_plan* plan, const float* knots, const float* ctrl,
@@ -286,6 +292,10 @@ nurbs_status nurbs_fit_step(const nurbs_plan* plan, const float* knots, float* c
  *   - The first call on a device looks up the array's device address (once per
  *     device, with that device current); make that first call before any stream
  *     capture.
+ *   - Device-side data errors (knots, domain, sample order) go to an error word
+ *     at the head of the array, which calls do not clear: it collects the checks
+ *     of every call until nurbs_noalloc_get_error reads it.  nurbs_plan_get_error
+ *     does not see them (it reads a plan's bound workspace).
  */
 #define NURBS_NOALLOC_SCRATCH_BYTES (8u << 20)
 
@@ -293,6 +303,16 @@ nurbs_status nurbs_mse_fwd_bwd_noalloc(const nurbs_plan* plan, const float* knot
                                        const float* params, const float* target, float* pts,
                                        float* grad_ctrl, float* grad_knots, float* loss_items,
                                        float grad_scale, nurbs_stream_t stream);
+
+/*
+ * nurbs_noalloc_get_error -- the nurbs_plan_get_error of nurbs_mse_fwd_bwd_noalloc
+ * (no counterpart in the paper either): synchronise `stream`, read and clear the
+ * error word of the allocation-free entry point's fixed array on the current
+ * device.  *flags (may be NULL) receives the raw bit set collected by every
+ * allocation-free call since the last read; returns the lowest raised status, or
+ * NURBS_OK.  Allocates nothing.  Errors: NURBS_ERR_CUDA.
+ */
+nurbs_status nurbs_noalloc_get_error(nurbs_stream_t stream, uint32_t* flags);
 
 
 /*

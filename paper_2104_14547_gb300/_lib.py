@@ -79,7 +79,7 @@ class NurbsError(RuntimeError):
 class Desc(ctypes.Structure):
     _fields_ = [("p", ctypes.c_int32), ("q", ctypes.c_int32), ("n1", ctypes.c_int32), ("m1", ctypes.c_int32),
                 ("nu", ctypes.c_int32), ("nv", ctypes.c_int32), ("adam_step", ctypes.c_int32),
-                ("reserved1", ctypes.c_int32), ("knot_u", ctypes.c_int64), ("knot_v", ctypes.c_int64),
+                ("grad_scale", ctypes.c_float), ("knot_u", ctypes.c_int64), ("knot_v", ctypes.c_int64),
                 ("ctrl", ctypes.c_int64), ("param_u", ctypes.c_int64), ("param_v", ctypes.c_int64),
                 ("pts", ctypes.c_int64)]
 
@@ -117,6 +117,7 @@ SIGNATURES = {
     "nurbs_backward": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "nurbs_mse_fwd_bwd": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _f, _vp]),
     "nurbs_mse_fwd_bwd_noalloc": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _f, _vp]),
+    "nurbs_noalloc_get_error": (_i32, [_vp, ctypes.POINTER(ctypes.c_uint32)]),
     "nurbs_fit_step": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.POINTER(Adam), _i32, _f, _vp, _vp, _vp]),
     "nurbs_chamfer": (_i32, [_i32, _vp, _vp, _i32, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                              _i64, _i64, _vp]),

@@ -32,7 +32,7 @@ class Packed:
 
 
 DESC_DTYPE = np.dtype([("p", "<i4"), ("q", "<i4"), ("n1", "<i4"), ("m1", "<i4"), ("nu", "<i4"), ("nv", "<i4"),
-                       ("adam_step", "<i4"), ("r1", "<i4"), ("knot_u", "<i8"), ("knot_v", "<i8"), ("ctrl", "<i8"),
+                       ("adam_step", "<i4"), ("grad_scale", "<f4"), ("knot_u", "<i8"), ("knot_v", "<i8"), ("ctrl", "<i8"),
                        ("param_u", "<i8"), ("param_v", "<i8"), ("pts", "<i8")])
 assert DESC_DTYPE.itemsize == ctypes.sizeof(_lib.Desc)
 
@@ -124,14 +124,31 @@ def _stream(stream=None):
     return ctypes.c_void_p(s.cuda_stream)
 
 
+def item_mean_scales(descs: np.ndarray) -> np.ndarray:
+    """A copy of `descs` whose items each carry grad_scale = 2 / (3 * its own point
+    count): the MSE of every item is then the mean over its own points (Sec. 4,
+    Eq. 12), and its gradient and Adam trajectory do not depend on which other
+    items share the batch.  Items without points keep 0."""
+    d = np.array(descs, dtype=DESC_DTYPE, copy=True)
+    npts = d["nu"].astype(np.int64) * np.where(d["nv"] > 0, d["nv"], 1)
+    d["grad_scale"] = np.where(npts > 0, (2.0 / (3.0 * np.maximum(npts, 1))).astype(np.float32), np.float32(0))
+    return d
+
+
 class Plan:
-    """A libnurbs plan for one batch layout plus its device workspace."""
+    """A libnurbs plan for one batch layout plus its device workspace.
+
+    item_mean=True gives every item its own loss normalisation (item_mean_scales):
+    the grad_scale argument of mse_fwd_bwd / fit_step then only applies to items
+    whose descriptor scale is 0 (none, after item_mean_scales)."""
 
     def __init__(self, kind: int, descs: np.ndarray, device="cuda", rows: int = 0, warps: int = 0,
-                 ctas_per_sm: int = 0, max_ctas: int = 0):
+                 ctas_per_sm: int = 0, max_ctas: int = 0, item_mean: bool = False, workspace=None):
         self.lib = _lib.load()
         self.kind = kind
         self.descs = np.ascontiguousarray(descs, dtype=DESC_DTYPE)
+        if item_mean:
+            self.descs = item_mean_scales(self.descs)
         self.count = len(self.descs)
         self.warps = warps if warps > 0 else 8     # the library's default
         cfg = _lib.TileCfg(rows, warps, ctas_per_sm, max_ctas)
@@ -145,7 +162,15 @@ class Plan:
         self.points = int(self.lib.nurbs_plan_points(h))
         self.tiles = int(self.lib.nurbs_plan_tiles(h))
         self.device = torch.device(device)
-        self.workspace = torch.zeros(max(self.ws_bytes, 256), dtype=torch.uint8, device=self.device)
+        if workspace is not None:
+            # a caller-owned (e.g. pooled) buffer: it must be a large enough uint8 device tensor;
+            # bind uploads the tables and clears the counters, the rest needs no clearing
+            if (not isinstance(workspace, torch.Tensor) or workspace.dtype != torch.uint8 or not workspace.is_cuda
+                    or workspace.numel() < self.ws_bytes):
+                raise ValueError(f"workspace must be a uint8 device tensor of at least {self.ws_bytes} bytes")
+            self.workspace = workspace
+        else:
+            self.workspace = torch.zeros(max(self.ws_bytes, 256), dtype=torch.uint8, device=self.device)
         _lib.check(self.lib.nurbs_plan_bind(h, _ptr(self.workspace), self.workspace.numel(), _stream()),
                    "nurbs_plan_bind")
 

@@ -1,6 +1,7 @@
 // C-ABI of libnurbs: planning (tiling a ragged batch, workspace layout),
 // binding a workspace, and the execution entry points declared in nurbs.h.
 #include <algorithm>
+#include <cstddef>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -79,6 +80,7 @@ nurbs_status check_desc(int32_t kind, const nurbs_desc& d)
     if (d.p < 1 || d.p > NURBS_MAX_DEGREE || d.n1 < d.p + 1) return NURBS_ERR_DEGREE;
     if (d.n1 > NURBS_MAX_CTRL) return NURBS_ERR_SIZE;
     if (d.knot_u < 0 || d.ctrl < 0 || d.param_u < 0 || d.pts < 0) return NURBS_ERR_ARG;
+    if (!(d.grad_scale >= 0.f) || !std::isfinite(d.grad_scale)) return NURBS_ERR_ARG;
     if (kind == NURBS_KIND_SURFACE) {
         if (d.nv < 0 || d.m1 <= 0) return NURBS_ERR_ARG;
         if (d.q < 1 || d.q > NURBS_MAX_DEGREE || d.m1 < d.q + 1) return NURBS_ERR_DEGREE;
@@ -103,6 +105,7 @@ ItemDev make_item(int32_t kind, const nurbs_desc& d)
         it.param_u = d.param_u; it.param_v = d.param_v; it.pts = d.pts; it.curve = 0;
     }
     it.adam_step = d.adam_step > 0 ? d.adam_step : 0;
+    it.gscale = d.grad_scale;
     return it;
 }
 
@@ -159,12 +162,20 @@ nurbs_status nurbs_plan_create(int32_t kind, const nurbs_desc* h_desc, int32_t c
         it.ck = (kind == NURBS_KIND_CURVE && it.m1 <= kCurveCtrlCap) ? 1 : 0;
         if (it.ck) pl->c_mc = std::max(pl->c_mc, it.m1);
     }
+    // Within a group, items enter the queue longest first (most samples; ties in
+    // item order), so the persistent CTAs end on short items rather than waiting
+    // on one long item at the tail.  Results do not depend on the order.
+    std::vector<int32_t> order(count);
+    for (int32_t k = 0; k < count; ++k) order[k] = k;
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+        return (int64_t)pl->items[a].nu * pl->items[a].nv > (int64_t)pl->items[b].nu * pl->items[b].nv;
+    });
     for (int q = 1; q <= NURBS_MAX_DEGREE; ++q) {
         PlanGroup grp;
         grp.p = 0; grp.q = q; grp.ck = 1;
         grp.t0 = (int)pl->tiles.size();
         for (int v = 0; v < 6; ++v) grp.grid[v] = 0;
-        for (int32_t k = 0; k < count; ++k) {
+        for (int32_t k : order) {
             ItemDev& it = pl->items[k];
             if (!it.ck || it.q != q) continue;
             it.first_tile = (int)pl->tiles.size();
@@ -192,7 +203,7 @@ nurbs_status nurbs_plan_create(int32_t kind, const nurbs_desc* h_desc, int32_t c
         grp.p = gp; grp.q = gq; grp.ck = 0;
         grp.t0 = (int)pl->tiles.size();
         for (int v = 0; v < 6; ++v) grp.grid[v] = 0;
-        for (int32_t k = 0; k < count; ++k) {
+        for (int32_t k : order) {
             ItemDev& it = pl->items[k];
             if (it.p != gp || it.q != gq || it.ck) continue;
             it.first_tile = (int)pl->tiles.size();
@@ -675,7 +686,9 @@ int32_t nurbs_last_cuda_error(void) { return g_last_cuda_error; }
 // this one entry point is a fixed array in the library's device image.  Every
 // call shares it, so each call re-uploads the plan's item and tile tables into it
 // and clears the queue/arrival counters before launching; the partial-sum slots
-// need no clearing (every slot is written before it is read).
+// need no clearing (every slot is written before it is read).  The error word at
+// the head of the array is not cleared by a call: it collects the device checks
+// of every call until nurbs_noalloc_get_error reads and clears it.
 // ---------------------------------------------------------------------------
 namespace {
 
@@ -721,8 +734,10 @@ extern "C" nurbs_status nurbs_mse_fwd_bwd_noalloc(const nurbs_plan* cpl, const f
     nurbs_plan* pl = const_cast<nurbs_plan*>(cpl);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     unsigned char* ws = static_cast<unsigned char*>(scratch);
-    // tables from the plan's host copies; header and arrival counters cleared
-    cudaError_t e = cudaMemsetAsync(ws, 0, pl->items_off, s);
+    // tables from the plan's host copies; queue and arrival counters cleared (the
+    // error word, the header's first 4 bytes, keeps what earlier calls raised)
+    static_assert(offsetof(WsHeader, error) == 0 && sizeof(((WsHeader*)nullptr)->error) == 4, "error word");
+    cudaError_t e = cudaMemsetAsync(ws + 4, 0, pl->items_off - 4, s);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(ws + pl->items_off, pl->items.data(), sizeof(ItemDev) * pl->items.size(),
                             cudaMemcpyHostToDevice, s);
@@ -745,5 +760,24 @@ extern "C" nurbs_status nurbs_mse_fwd_bwd_noalloc(const nurbs_plan* cpl, const f
     kp.loss_items = loss_items;
     kp.grad_scale = grad_scale;
     const int v = grad_knots != nullptr ? 4 : 3;
-    return launch_groups(pl, v, kp, ws, s, false);
+    // the same launch shape as nurbs_mse_fwd_bwd (CTA cap included)
+    return launch_groups(pl, v, kp, ws, s, true);
+}
+
+extern "C" nurbs_status nurbs_noalloc_get_error(nurbs_stream_t stream, uint32_t* flags)
+{
+    void* scratch = nullptr;
+    nurbs_status st = noalloc_scratch(&scratch);
+    if (st != NURBS_OK) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    uint32_t word = 0;
+    cudaError_t e = cudaMemcpyAsync(&word, scratch, 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(scratch, 0, 4, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (flags) *flags = word;
+    for (int b = 1; b < 32; ++b)
+        if (word & (1u << b)) return (nurbs_status)b;
+    return NURBS_OK;
 }

@@ -167,6 +167,7 @@ __device__ __forceinline__ void curve_body(const KParams& kp, int t, unsigned ch
 #pragma unroll
     for (int k = 0; k < (KW > 0 ? KW : 1); ++k) kacc[k] = 0.f;
     float lossacc = 0.f, uprev = -3.0e38f;
+    const float gsc = it.gscale > 0.f ? it.gscale : kp.grad_scale;   // the item's own dL/dS scale, if set
     int cur = -1;
 
     auto retire_row = [&](int i, float4 v) {
@@ -246,7 +247,7 @@ __device__ __forceinline__ void curve_body(const KParams& kp, int t, unsigned ch
         if constexpr (MSE) {
             gx = Sx - gx; gy = Sy - gy; gz = Sz - gz;
             lossacc = fmaf(gx, gx, fmaf(gy, gy, fmaf(gz, gz, lossacc)));
-            ginv *= kp.grad_scale;
+            ginv *= gsc;
         }
         const float lx = gx * ginv, ly = gy * ginv, lz = gz * ginv;
         const float4 lam = make_float4(lx, ly, lz, -fmaf(Sx, lx, fmaf(Sy, ly, Sz * lz)));

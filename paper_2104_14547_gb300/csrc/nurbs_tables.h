@@ -44,6 +44,8 @@ struct ItemDev {
     int adam_step;   // fit step: this item's Adam step (0 = the launch's)
     int smemA;       // single-tile item whose homogeneous adjoint stays in shared memory
     int ck;          // curve run by the curve kernels (one warp per curve, one tile)
+    float gscale;    // MSE / fit step: this item's dL/dS scale (0 = the launch's)
+    int pad_;
     long long knot_u, knot_v, ctrl, param_u, param_v, pts;
 };
 

@@ -620,6 +620,7 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
     float* uslot = GRAD ? slot + it.wbase + (long long)wr * it.unit_slot : nullptr;
 
     float lossacc = 0.f;
+    const float gsc = it.gscale > 0.f ? it.gscale : kp.grad_scale;   // the item's own dL/dS scale, if set
     float Gam[QB];
 #pragma unroll
     for (int h = 0; h < QB; ++h) Gam[h] = 0.f;
@@ -921,7 +922,7 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
                         if (!full) { dx = cvalid ? dx : 0.f; dy = cvalid ? dy : 0.f; dz = cvalid ? dz : 0.f; }
                         lossacc = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, lossacc)));
                         gx = dx; gy = dy; gz = dz;
-                        ginv *= kp.grad_scale;
+                        ginv *= gsc;
                     } else if (full) {
                         gx = gp[0]; gy = gp[1]; gz = gp[2];
                     } else {

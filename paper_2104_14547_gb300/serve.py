@@ -7,15 +7,29 @@ the free HBM at start-up; registering a model succeeds only while it has room
 
 * ``eval``  -- evaluate the model's current surface on its grid; the points come back;
 * ``fit``   -- one fused step (forward, MSE against the stored target, backward,
-  Adam update of the control net in place); the loss comes back.
+  Adam update of the control net in place); the loss comes back.  The loss of a
+  fit request is the mean over its own model's points (Sec. 4, Eq. 12): each
+  item of a fit wave carries its own gradient scale, so a model's trajectory is
+  the same whichever requests share its waves;
+* ``checkpoint`` / ``restore`` -- barriers in arrival order: the scheduler lets
+  the waves in flight finish, then copies every model's control net, Adam moments
+  and step count to host memory (``checkpoint``, the result) or back
+  (``restore``, ``Request.payload`` = a checkpoint), so that a fit after a
+  restore continues bit for bit where the checkpoint left off.
+
+A request can be cancelled (``Request.cancel``) until a wave admits it; it then
+completes at once with ``error == "cancelled"`` and never reaches the GPU.  Once
+admitted it runs to completion.
 
 A scheduler thread forms waves from the pending requests in arrival order.  A
 wave holds at most one request per model and as many evaluations as the output
 region has room for; requests that do not fit wait for the next wave.  Each wave
 is one libnurbs plan per kind (eval / fit) launched on its own stream; up to two
 waves are in flight at once, so requests that arrive while a wave runs start on
-the device before it finishes.  Every request records its latency (submit to
-result on the host).
+the device before it finishes.  The plans bind to workspaces kept in a pool (one
+per wave slot and kind, grown when a wave needs more), so forming a wave
+allocates no device memory.  Every request records its latency (submit to result
+on the host).
 """
 from __future__ import annotations
 
@@ -86,17 +100,23 @@ class Model:
 
 @dataclass
 class Request:
-    kind: str                 # "eval" or "fit"
-    model: int
+    kind: str                 # "eval", "fit", "checkpoint" or "restore"
+    model: int = -1
     t_submit: float = 0.0
     t_done: float = 0.0
     result: object = None
-    error: str | None = None  # set when the server failed the request
+    error: str | None = None  # set when the server failed (or cancelled) the request
+    payload: object = None    # "restore": the checkpoint to put back
+    cancelled: bool = False
     done: threading.Event = field(default_factory=threading.Event)
 
     @property
     def latency(self) -> float:
         return self.t_done - self.t_submit
+
+    def cancel(self):
+        """Withdraw the request; takes effect if no wave has admitted it yet."""
+        self.cancelled = True
 
 
 class Server:
@@ -131,6 +151,9 @@ class Server:
         self.lr = lr
         self.tile = dict(warps=warps, rows=rows)
         self.streams = [(torch.cuda.Stream(self.device), torch.cuda.Stream(self.device)) for _ in range(2)]
+        # plan workspaces, one per (wave slot, kind): reused by every wave on that slot
+        self.ws_pool = {(slot, kind): torch.zeros(1 << 20, dtype=torch.uint8, device=self.device)
+                        for slot in range(2) for kind in ("eval", "fit")}
         self.queue: collections.deque[Request] = collections.deque()
         self.cv = threading.Condition()
         self.running = False
@@ -195,10 +218,17 @@ class Server:
 
     def _form_wave(self, busy: set):
         """Pending requests admitted into one wave (arrival order, one per model,
-        evaluation outputs while the output region has room)."""
+        evaluation outputs while the output region has room).  Stops at a
+        checkpoint or restore barrier, which runs on its own."""
         evals, fits, out_used, keep = [], [], 0, collections.deque()
         while self.queue and len(evals) + len(fits) < self.max_wave:
             r = self.queue.popleft()
+            if r.cancelled:
+                self._finish_cancelled(r)
+                continue
+            if r.kind in ("checkpoint", "restore"):
+                keep.append(r)
+                break
             m = self.models[r.model]
             if r.model in busy:
                 keep.append(r)
@@ -217,21 +247,42 @@ class Server:
             self.queue.appendleft(keep.pop())
         return evals, fits
 
+    @staticmethod
+    def _finish_cancelled(r: Request):
+        r.error = "cancelled"
+        r.t_done = time.perf_counter()
+        r.done.set()
+
     def _descs(self, entries, fit: bool):
         d = np.zeros(len(entries), batch.DESC_DTYPE)
         for k, e in enumerate(entries):
             r, off = (e, None) if fit else e
             m = self.models[r.model]
-            d[k] = (m.p, m.q, m.n1, m.m1, m.nu, m.nv, (m.steps + 1) if fit else 0, 0,
+            # a fit item's loss is the mean over its own points: grad_scale 2 / (3 nu nv)
+            gs = np.float32(2.0 / (3.0 * max(m.nu * m.nv, 1))) if fit else 0.0
+            d[k] = (m.p, m.q, m.n1, m.m1, m.nu, m.nv, (m.steps + 1) if fit else 0, gs,
                     m.knot_u, m.knot_v, m.ctrl, m.param_u, m.param_v, m.target if fit else off)
         return d
+
+    def _plan(self, slot, kind, descs):
+        """A plan bound to the pooled workspace of (slot, kind), grown if it is too small."""
+        plan = None
+        key = (slot, kind)
+        try:
+            plan = batch.Plan(_lib.KIND_SURFACE, descs, device=self.device, workspace=self.ws_pool[key],
+                              **self.tile)
+        except ValueError:
+            probe = batch.Plan(_lib.KIND_SURFACE, descs, device=self.device, workspace=None, **self.tile)
+            self.ws_pool[key] = probe.workspace
+            plan = probe
+        return plan
 
     def _launch(self, slot, evals, fits):
         se, sf = self.streams[slot]
         main = torch.cuda.current_stream(self.device)
-        # plans first: their workspaces are cleared and bound on the current stream
-        pe = batch.Plan(_lib.KIND_SURFACE, self._descs(evals, False), device=self.device, **self.tile) if evals else None
-        pf = batch.Plan(_lib.KIND_SURFACE, self._descs(fits, True), device=self.device, **self.tile) if fits else None
+        # plans first: their tables are uploaded into the pooled workspaces on the current stream
+        pe = self._plan(slot, "eval", self._descs(evals, False)) if evals else None
+        pf = self._plan(slot, "fit", self._descs(fits, True)) if fits else None
         se.wait_stream(main)
         sf.wait_stream(main)
         plans = []
@@ -243,9 +294,9 @@ class Server:
                 self.host_out[slot][:n_out].copy_(self.out[slot][:n_out], non_blocking=True)
             plans.append(pe)
         if fits:
-            npts = sum(self.models[r.model].nu * self.models[r.model].nv for r in fits)
+            # every item carries its own grad_scale and Adam step (see _descs)
             pf.fit_step(self.scalars, self.ctrl, self.scalars, self.target, self.adam_m, self.adam_v, 1,
-                        lr=self.lr, loss_items=self.loss[slot], grad_scale=2.0 / (3.0 * max(npts, 1)), stream=sf)
+                        lr=self.lr, loss_items=self.loss[slot], stream=sf)
             with torch.cuda.stream(sf):
                 self.host_loss[slot][: len(fits)].copy_(self.loss[slot][: len(fits)], non_blocking=True)
             plans.append(pf)
@@ -295,6 +346,44 @@ class Server:
                     r.error = self.failure
                     r.done.set()
 
+    # ------------------------------------------------------------ checkpoint / restore
+    def _checkpoint(self) -> dict:
+        """Host copies of every model's control net, Adam moments and step count
+        (run by the scheduler with no wave in flight)."""
+        ck = {"models": {}}
+        for mid, m in self.models.items():
+            n = m.n1 * m.m1
+            ck["models"][mid] = dict(ctrl=self.ctrl[m.ctrl: m.ctrl + n].cpu(),
+                                     adam_m=self.adam_m[m.ctrl: m.ctrl + n].cpu(),
+                                     adam_v=self.adam_v[m.ctrl: m.ctrl + n].cpu(), steps=m.steps)
+        return ck
+
+    def _restore(self, ck: dict):
+        for mid, st in ck["models"].items():
+            m = self.models[mid]
+            n = m.n1 * m.m1
+            if st["ctrl"].shape[0] != n:
+                raise ValueError(f"checkpoint of model {mid} does not match its control net")
+            self.ctrl[m.ctrl: m.ctrl + n] = st["ctrl"].to(self.device)
+            self.adam_m[m.ctrl: m.ctrl + n] = st["adam_m"].to(self.device)
+            self.adam_v[m.ctrl: m.ctrl + n] = st["adam_v"].to(self.device)
+            m.steps = int(st["steps"])
+        torch.cuda.synchronize(self.device)
+
+    def checkpoint(self, timeout: float = 60.0) -> dict:
+        """Snapshot of every model's device-resident state, taken after the
+        requests submitted before this call (a barrier in arrival order)."""
+        r = self.submit(Request("checkpoint"))
+        if not r.done.wait(timeout) or r.error is not None:
+            raise RuntimeError(f"checkpoint failed: {r.error or 'timeout'}")
+        return r.result
+
+    def restore(self, ck: dict, timeout: float = 60.0):
+        """Put a checkpoint back (a barrier in arrival order, like checkpoint)."""
+        r = self.submit(Request("restore", payload=ck))
+        if not r.done.wait(timeout) or r.error is not None:
+            raise RuntimeError(f"restore failed: {r.error or 'timeout'}")
+
     def _serve(self):
         torch.cuda.set_device(self.device)
         inflight: collections.deque = collections.deque()
@@ -302,12 +391,28 @@ class Server:
         busy: set = set()
         slot = 0
         while True:
+            barrier = None
             with self.cv:
                 while self.running and not self.queue and not inflight:
                     self.cv.wait(timeout=0.05)
                 if not self.running and not self.queue and not inflight:
                     return
                 wave = self._form_wave(busy) if len(inflight) < 2 and self.queue else ([], [])
+                if not (wave[0] or wave[1]) and not inflight and self.queue and \
+                        self.queue[0].kind in ("checkpoint", "restore"):
+                    barrier = self.queue.popleft()
+            if barrier is not None:
+                # every earlier wave has finished: the arena holds their results
+                if barrier.cancelled:
+                    self._finish_cancelled(barrier)
+                    continue
+                if barrier.kind == "checkpoint":
+                    barrier.result = self._checkpoint()
+                else:
+                    self._restore(barrier.payload)
+                barrier.t_done = time.perf_counter()
+                barrier.done.set()
+                continue
             evals, fits = wave
             if evals or fits:
                 self._inflight_requests = [r for r, _ in evals] + list(fits) + \

@@ -68,6 +68,13 @@ def test_planner_rejects_bad_descriptors():
     d["nu"] = -1
     assert _plan(_lib.KIND_SURFACE, d)[0] == 1
     assert _plan(7, pk.descs)[0] == 1                    # kind
+    for bad in (-1.0, float("nan"), float("inf")):        # an item's own loss scale
+        d = pk.descs.copy()
+        d["grad_scale"] = bad
+        assert _plan(_lib.KIND_SURFACE, d)[0] == 1
+    d = pk.descs.copy()
+    d["grad_scale"] = 1e-4
+    assert _plan(_lib.KIND_SURFACE, d)[0] == 0
     cfg = _lib.TileCfg(0, 9, 0, 0)                       # more warps than the kernels allow
     assert _plan(_lib.KIND_SURFACE, pk.descs, cfg)[0] == 1
     cfg = _lib.TileCfg(0, 8, 0, -1)                      # negative CTA cap

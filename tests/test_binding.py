@@ -57,3 +57,18 @@ def test_chamfer_refuses_bad_sizes_before_any_kernel():
         losses.chamfer(P, [5, 6], Q, [4, 4])
     with pytest.raises(ValueError, match="GPU"):
         losses.chamfer(P, [5, 5], Q, [4, 4])
+
+
+def test_item_mean_scales():
+    # every item's own MSE normalisation: 2 / (3 x its point count); empty items keep 0
+    rng = np.random.default_rng(1)
+    surfs = [synth.surface(rng, 3, 2, 6, 7, nu, nv) for nu, nv in ((10, 12), (0, 5), (7, 1))]
+    pk = batch.pack_surfaces(surfs)
+    d = batch.item_mean_scales(pk.descs)
+    assert d["grad_scale"].dtype == np.float32
+    assert d["grad_scale"][0] == np.float32(2.0 / (3 * 120)) and d["grad_scale"][1] == 0.0
+    assert d["grad_scale"][2] == np.float32(2.0 / 21)
+    assert np.all(pk.descs["grad_scale"] == 0.0)          # a copy: the packed batch is unchanged
+    curves = [synth.curve(rng, 3, 20, n) for n in (50, 0)]
+    cd = batch.item_mean_scales(batch.pack_curves(curves).descs)
+    assert cd["grad_scale"][0] == np.float32(2.0 / 150) and cd["grad_scale"][1] == 0.0

@@ -170,3 +170,146 @@ def test_plan_occupancy_reports_what_launches():
     curves, _ = synth.cubic_curve_batch(0, 8, 64, 256)
     cplan = batch.Plan.for_packed(batch.pack_curves(curves))
     assert cplan.occupancy("eval")[0] == 8 and cplan.occupancy("mse")[0] == 4
+
+
+def _server_models(srv, seed, n, twins=0):
+    """n random ragged-shaped models (and `twins` more that repeat the first ones:
+    same surface, same target), registered on srv."""
+    rng = np.random.default_rng(seed)
+    mids, surfs, targets = [], [], []
+    for k in range(n):
+        p, q = int(rng.integers(2, 6)), int(rng.integers(2, 6))
+        s = synth.surface(rng, p, q, int(rng.integers(p + 1, 20)), int(rng.integers(q + 1, 20)),
+                          int(rng.integers(8, 60)), int(rng.integers(8, 60)))
+        t = synth.twin_net(rng, s)
+        surfs.append(s)
+        targets.append(O.surface_eval(t.p, t.q, t.U, t.V, t.ctrl, t.u, t.v))
+    for k in range(n + twins):
+        mids.append(srv.register(surfs[k % n], targets[k % n]))
+    assert all(m is not None for m in mids)
+    return mids, surfs, targets
+
+
+def _model_state(srv, mid):
+    m = srv.models[mid]
+    n = m.n1 * m.m1
+    return (srv.ctrl[m.ctrl: m.ctrl + n].cpu().numpy(), srv.adam_m[m.ctrl: m.ctrl + n].cpu().numpy(),
+            srv.adam_v[m.ctrl: m.ctrl + n].cpu().numpy())
+
+
+def test_server_fits_same_alone_and_in_the_mix():
+    # models 0..3 fit alone (one request at a time); their twins 8..11 fit in the mix,
+    # interleaved with evaluations and fit steps of models 4..7, several per wave
+    srv = serve.Server(hbm_fraction=0.02, max_wave=64, out_points=1 << 20)
+    mids, surfs, targets = _server_models(srv, 45, 8, twins=4)
+    alone_ids, other_ids, mix_ids = mids[:4], mids[4:8], mids[8:12]
+    k_steps = 4
+    srv.start()
+    try:
+        alone_loss = {m: [] for m in alone_ids}
+        for _ in range(k_steps):
+            for m in alone_ids:
+                r = srv.submit(serve.Request("fit", m))
+                _wait(r)
+                alone_loss[m].append(r.result)
+        mix_reqs = {m: [] for m in mix_ids}
+        reqs = []
+        for step in range(k_steps):
+            for j, m in enumerate(mix_ids):
+                reqs.append(srv.submit(serve.Request("eval", other_ids[j])))
+                r = srv.submit(serve.Request("fit", m))
+                mix_reqs[m].append(r)
+                reqs.append(r)
+                reqs.append(srv.submit(serve.Request("fit", other_ids[(j + step) % 4])))
+        for r in reqs:
+            _wait(r)
+        for a, b in zip(alone_ids, mix_ids):
+            assert [r.result for r in mix_reqs[b]] == alone_loss[a]
+            for x, y in zip(_model_state(srv, a), _model_state(srv, b)):
+                assert np.array_equal(x, y)
+    finally:
+        srv.stop()
+
+
+def test_server_first_fit_matches_oracle_adam():
+    # one fit request = Adam step 1 on the gradient of the model's own mean squared error
+    srv = serve.Server(hbm_fraction=0.02, max_wave=64, out_points=1 << 20, lr=1e-3)
+    mids, surfs, targets = _server_models(srv, 46, 3)
+    srv.start()
+    try:
+        reqs = [srv.submit(serve.Request("fit", m)) for m in mids]
+        for r in reqs:
+            _wait(r)
+        for m, s, T, r in zip(mids, surfs, targets, reqs):
+            S = O.surface_eval(s.p, s.q, s.U, s.V, s.ctrl, s.u, s.v)
+            Tf = np.asarray(T, np.float32).astype(np.float64)
+            L, g = O.mse(S, Tf, 3 * s.npts)
+            assert abs(r.result - L) <= 1e-4 * L
+            dc, _, _ = O.surface_vjp(s.p, s.q, s.U, s.V, s.ctrl, s.u, s.v, g)
+            th, _, _ = O.adam(s.ctrl.astype(np.float64), dc, np.zeros_like(dc), np.zeros_like(dc), 1, lr=1e-3)
+            after = _model_state(srv, m)[0].reshape(th.shape)
+            # step 1 moves each component by lr * sign(g): compare where the sign is sure
+            sure = np.abs(dc) > 1e-2 * np.abs(dc).max()
+            assert np.abs(after - th)[sure].max(initial=0.0) <= 1e-6 + 1e-6 * np.abs(th).max()
+    finally:
+        srv.stop()
+
+
+def test_server_checkpoint_restore_continues_bit_for_bit():
+    srv = serve.Server(hbm_fraction=0.02, max_wave=64, out_points=1 << 20)
+    mids, _, _ = _server_models(srv, 47, 5)
+    srv.start()
+    try:
+        for _ in range(3):
+            rs = [srv.submit(serve.Request("fit", m)) for m in mids]
+            for r in rs:
+                _wait(r)
+        ck = srv.checkpoint()
+        rs = [srv.submit(serve.Request("fit", m)) for m in mids]
+        for r in rs:
+            _wait(r)
+        first = [(r.result, _model_state(srv, r.model)) for r in rs]
+        srv.restore(ck)
+        assert all(srv.models[m].steps == 3 for m in mids)
+        rs = [srv.submit(serve.Request("fit", m)) for m in mids]
+        for r in rs:
+            _wait(r)
+        for (loss, st), r in zip(first, rs):
+            assert r.result == loss
+            for x, y in zip(st, _model_state(srv, r.model)):
+                assert np.array_equal(x, y)
+    finally:
+        srv.stop()
+
+
+def test_server_cancelled_request_never_runs():
+    # a request withdrawn before admission completes as cancelled and leaves its model untouched
+    srv = serve.Server(hbm_fraction=0.02, max_wave=64, out_points=1 << 20)
+    mids, _, _ = _server_models(srv, 48, 2)
+    before = _model_state(srv, mids[0])
+    r = serve.Request("fit", mids[0])
+    r.cancel()
+    srv.submit(r)                       # queued before the scheduler starts
+    srv.start()
+    try:
+        assert r.done.wait(timeout=30.0)
+        assert r.error == "cancelled"
+        ok = srv.submit(serve.Request("eval", mids[1]))
+        _wait(ok)
+        assert srv.models[mids[0]].steps == 0
+        for x, y in zip(before, _model_state(srv, mids[0])):
+            assert np.array_equal(x, y)
+    finally:
+        srv.stop()
+
+
+def test_server_admission_refuses_when_arena_is_full():
+    # a tiny HBM share: registration succeeds while the arena has room, then refuses
+    srv = serve.Server(hbm_fraction=1e-9, max_wave=16, out_points=1 << 16)
+    rng = np.random.default_rng(49)
+    s = synth.surface(rng, 3, 3, 32, 32, 64, 64)
+    T = np.zeros((64, 64, 3))
+    got = [srv.register(s, T) for _ in range(80)]
+    admitted = [m for m in got if m is not None]
+    assert 0 < len(admitted) < len(got)
+    assert all(m is None for m in got[len(admitted):])   # once full, every later model is refused

@@ -2,17 +2,18 @@
 against the FP64 oracle.
 
 - The fused step on 256 bicubic 128x128 surfaces with the bench's tile (8 warps,
-  128 rows): every item's loss, control-point and knot gradients.
+  128 rows): every item's points (element by element), loss, control-point and
+  knot gradients.
 - The 4096-curve fit workload: every curve's MSE gradients, and the Adam update
   wherever the gradient is not near zero.  At step 1, Adam's step is lr * sign(g),
   so a component whose gradient is near zero can flip under FP32 rounding.
 - The 1000-surface ragged batch through the CUDA-graph engine, on a sample of
-  items across all degree groups."""
+  items across all degree groups: points, loss and gradients."""
 import numpy as np
 import pytest
 import torch
 
-from gpu_util import G_TOL, rel_inf
+from gpu_util import G_TOL, S_TOL, bbox_diag, rel_inf
 from oracle import oracle as O
 from paper_2104_14547_gb300 import batch, engine, synth
 
@@ -43,9 +44,13 @@ def test_bench_step_full_size():
     dcs = batch.unpack_ctrl(pk, gc.cpu().numpy())
     dks = batch.unpack_knots(pk, gk.cpu().numpy())
     lossn = loss.cpu().numpy()
-    worst = 0.0
+    Sg = batch.unpack_points(pk, pts.cpu().numpy())
+    worst = worst_s = 0.0
     for k, s in enumerate(surfs):
         S = O.surface_eval(s.p, s.q, s.U, s.V, s.ctrl, s.u, s.v)
+        es = np.abs(Sg[k].astype(np.float64) - S).max() / bbox_diag(s.ctrl)
+        worst_s = max(worst_s, es)
+        assert es <= S_TOL, (k, es)
         Tk = Tn[k].astype(np.float64)
         g = scale * (S - Tk)
         dc, dU, dV = O.surface_vjp(s.p, s.q, s.U, s.V, s.ctrl, s.u, s.v, g)
@@ -54,7 +59,7 @@ def test_bench_step_full_size():
         assert e <= G_TOL, (k, e)
         ref_loss = float(((S - Tk) ** 2).sum())
         assert abs(lossn[k] - ref_loss) <= 1e-4 * ref_loss, (k, lossn[k], ref_loss)
-    assert worst < G_TOL
+    assert worst < G_TOL and worst_s <= S_TOL
 
 
 def test_curve_fit_workload_full_size():
@@ -97,12 +102,14 @@ def test_ragged_engine_full_size_sample():
     Tn = batch.unpack_points(pk, T.cpu().numpy())
     dcs = batch.unpack_ctrl(pk, eng.grad_ctrl.cpu().numpy())
     dks = batch.unpack_knots(pk, eng.grad_knots.cpu().numpy())
+    Sg = batch.unpack_points(pk, eng.pts.cpu().numpy())
     losses = eng.item_losses()
     rng = np.random.default_rng(0)
     sample = sorted(set(rng.choice(len(surfs), 24, replace=False).tolist()) | {0, len(surfs) - 1})
     for k in sample:
         s = surfs[k]
         S = O.surface_eval(s.p, s.q, s.U, s.V, s.ctrl, s.u, s.v)
+        assert np.abs(Sg[k].astype(np.float64) - S).max() <= S_TOL * bbox_diag(s.ctrl), (k, "points")
         Tk = Tn[k].astype(np.float64)
         g = eng.grad_scale * (S - Tk)
         dc, dU, dV = O.surface_vjp(s.p, s.q, s.U, s.V, s.ctrl, s.u, s.v, g)

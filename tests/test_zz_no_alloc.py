@@ -1,8 +1,10 @@
 """The allocation-free entry point nurbs_mse_fwd_bwd_noalloc, for callers that
 cannot allocate device memory (its scratch is a fixed array inside the library).
 It must give the results of nurbs_mse_fwd_bwd, call after call, through the
-C-ABI.  This file is collected last so that a run stopping at the first failure
-has already run every other test."""
+C-ABI: the same kernels, tiles and summation order, so the same bits (which is
+also within the parity tolerances).  Its device-side checks must be visible
+through nurbs_noalloc_get_error.  This file is collected last so that a run
+stopping at the first failure has already run every other test."""
 import ctypes
 
 import numpy as np
@@ -28,8 +30,15 @@ def _call_noalloc(lib, plan, kn, ct, pr, T, pts, gc, gk, loss, scale):
                                          ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
 
 
+def _noalloc_error(lib):
+    flags = ctypes.c_uint32(0)
+    st = lib.nurbs_noalloc_get_error(ctypes.c_void_p(torch.cuda.current_stream().cuda_stream), ctypes.byref(flags))
+    return int(st), int(flags.value)
+
+
 def test_noalloc_matches_workspace_entry_point_twice():
     lib = _lib.load()
+    _noalloc_error(lib)   # whatever earlier allocation-free calls left in the error word
     surfs, tg = synth.bicubic_batch(21, batch=12, net=16, grid=70)
     surfs.append(synth.surface(np.random.default_rng(22), 2, 4, 9, 11, 33, 150))   # another degree group, 2 warps
     tg.append(synth.twin_net(np.random.default_rng(23), surfs[-1]))
@@ -52,6 +61,9 @@ def test_noalloc_matches_workspace_entry_point_twice():
         st = _call_noalloc(lib, plan, kn, ct, pr, Td, out["pts"], out["gc"], out["gk"], out["loss"], scale)
         assert st == 0, _lib.status_string(st)
         torch.cuda.synchronize()
+        assert _noalloc_error(lib) == (0, 0)
+        for key in ref:   # same kernels, tiles and summation order as the workspace call: same bits
+            assert torch.equal(out[key], ref[key]), key
         S_ref = batch.unpack_points(pk, ref["pts"].cpu().numpy())
         S_new = batch.unpack_points(pk, out["pts"].cpu().numpy())
         for s, a, b in zip(surfs, S_ref, S_new):
@@ -74,3 +86,35 @@ def test_noalloc_rejects_plans_beyond_its_scratch():
     buf = torch.zeros((pk.npts, 3), device="cuda")
     st = _call_noalloc(lib, plan, kn, ct, pr, buf, None, torch.zeros_like(ct), None, None, 1.0)
     assert st == 6   # NURBS_ERR_WORKSPACE, before any GPU work
+
+
+def test_noalloc_reports_device_checks():
+    # samples out of order in one item: the kernels flag NURBS_ERR_ORDER in the fixed
+    # array's error word, which nurbs_noalloc_get_error reads and clears
+    lib = _lib.load()
+    _noalloc_error(lib)
+    rng = np.random.default_rng(25)
+    good = synth.surface(rng, 3, 3, 10, 10, 24, 24)
+    s = synth.surface(rng, 3, 3, 8, 8, 20, 20)
+    unsorted = synth.Surface(s.p, s.q, s.U, s.V, s.ctrl, s.u[::-1].copy(), s.v)
+    pk = batch.pack_surfaces([good, unsorted])
+    plan = batch.Plan.for_packed(pk)
+    kn, ct, pr = batch.to_device(pk)
+    T = torch.zeros((pk.npts, 3), device="cuda")
+    pts, gc, gk = torch.zeros_like(T), torch.zeros_like(ct), torch.zeros_like(kn)
+    loss = torch.zeros(pk.count, device="cuda")
+    for _ in range(2):   # the word collects the checks of every call until it is read
+        st = _call_noalloc(lib, plan, kn, ct, pr, T, pts, gc, gk, loss, 1.0)
+        assert st == 0, _lib.status_string(st)
+    st, flags = _noalloc_error(lib)
+    assert st == 5 and flags & (1 << 5), (st, flags)      # NURBS_ERR_ORDER
+    assert _noalloc_error(lib) == (0, 0)                  # read and cleared
+    assert plan.get_error() == (0, 0)                     # the plan's own workspace saw nothing
+    # a clean call afterwards reports nothing
+    clean = batch.pack_surfaces([good])
+    cplan = batch.Plan.for_packed(clean)
+    ckn, cct, cpr = batch.to_device(clean)
+    CT = torch.zeros((clean.npts, 3), device="cuda")
+    st = _call_noalloc(lib, cplan, ckn, cct, cpr, CT, torch.zeros_like(CT), torch.zeros_like(cct), None, None, 1.0)
+    assert st == 0
+    assert _noalloc_error(lib) == (0, 0)
