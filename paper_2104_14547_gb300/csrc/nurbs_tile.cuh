@@ -244,23 +244,34 @@ __device__ __forceinline__ void finish_ctrl(const KParams& kp, const ItemDev& it
     finish_point(kp, idx, c, a, mm, vv, lr_t, isb2);
 }
 
-// The only tile of its item, with A kept in shared memory: the net block holds,
-// for each control row, the first covering unit's block, and the overflow block
-// of unit u (pb rows from its first row) its share of rows an earlier unit also
-// covers.  s_units[3u..3u+2] = first control row, row count and the last control
-// row of the earlier units; columns [jlo, jlo+cw) were written.  Units are added
-// in order and every control point is finished; s_net, when not null, is the
-// item's control net staged in shared memory.  Each thread handles four points
-// per pass with all their loads issued first.
+// The only tile of its item, with A kept in shared memory.  The net block (zeroed
+// before the tile's rows) holds, for each control row, what its first covering
+// unit wrote; the overflow block of unit u (pb rows from its first row) holds its
+// share of rows an earlier unit also covers.  s_units[3u..3u+2] = first control
+// row, row count and the last control row of the earlier units; columns
+// [jlo, jlo+cw) were written.  The overflow rows are added into the net block in
+// unit order, then every control point is finished (its Cartesian point read from
+// global memory), four per thread per pass with their loads issued first.
 __device__ __forceinline__ void final_ctrl_smem(const KParams& kp, const ItemDev& it, int nwr, int pb,
-                                                const int* s_units, int jlo, int cw, const float4* s_net)
+                                                const int* s_units, int jlo, int cw)
 {
     extern __shared__ float4 smem4[];
     unsigned char* smem = reinterpret_cast<unsigned char*>(smem4);
     if (kp.grad_ctrl == nullptr && !kp.fit) return;
     const int m1 = it.m1, ncp = it.n1 * m1, bs = blockDim.x;
-    const float4* sB = reinterpret_cast<const float4*>(smem + kp.off_sa);
+    float4* sB = reinterpret_cast<float4*>(smem + kp.off_sa);
     const float4* sO = sB + ncp;
+    for (int u = 1; u < nwr; ++u) {
+        const int ilo = s_units[3 * u], nr = s_units[3 * u + 1], pm = s_units[3 * u + 2];
+        const int nov = nr > 0 ? max(0, min(ilo + nr - 1, pm) - ilo + 1) : 0;
+        for (int x = threadIdx.x; x < nov * cw; x += bs) {
+            const int ii = x / cw, jj = x - ii * cw;
+            float4& d = sB[(ilo + ii) * m1 + jlo + jj];
+            const float4 v = sO[(u * pb + ii) * m1 + jlo + jj];
+            d.x += v.x; d.y += v.y; d.z += v.z; d.w += v.w;
+        }
+        __syncthreads();
+    }
     float lr_t, isb2;
     adam_corrections(kp, it, lr_t, isb2);
     constexpr int EB = 4;
@@ -272,24 +283,9 @@ __device__ __forceinline__ void final_ctrl_smem(const KParams& kp, const ItemDev
             a[k] = c[k] = mm[k] = vv[k] = f4zero();
             if (e >= ncp) continue;
             const long long idx = it.ctrl + e;
-            c[k] = s_net != nullptr ? s_net[e] : kp.ctrl[idx];
+            c[k] = kp.ctrl[idx];
+            a[k] = sB[e];
             if (kp.fit) { mm[k] = kp.adam_m[idx]; vv[k] = kp.adam_v[idx]; }
-            const int i = e / m1, j = e - i * m1;
-            if (j >= jlo && j < jlo + cw) {
-                bool cov = false;
-                for (int u = 0; u < nwr; ++u) {
-                    const int ilo = s_units[3 * u], nr = s_units[3 * u + 1];
-                    cov |= nr > 0 && i >= ilo && i < ilo + nr;
-                }
-                if (cov) a[k] = sB[e];
-                for (int u = 1; u < nwr; ++u) {
-                    const int ilo = s_units[3 * u], nr = s_units[3 * u + 1], pm = s_units[3 * u + 2];
-                    if (nr > 0 && i >= ilo && i < ilo + nr && i <= pm) {
-                        const float4 v = sO[(u * pb + i - ilo) * m1 + j];
-                        a[k].x += v.x; a[k].y += v.y; a[k].z += v.z; a[k].w += v.w;
-                    }
-                }
-            }
         }
 #pragma unroll
         for (int k = 0; k < EB; ++k) {
@@ -466,27 +462,29 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
     const float* grow0 = GRAD ? kp.gin + 3 * prow0 : nullptr;
     const bool al16 = ((prow0 & 3) == 0) && ((it.nv & 3) == 0) && ((nvw & 3) == 0);
     const bool wrows = !empty && wr < nwr && ra < rb;
-    // requests go out in row order: src walks the rows, dst walks the ring slots
+    // Requests go out in row order, one commit group per row (empty past the unit's
+    // rows): the first kRing rows before the prologue, then each step refills the
+    // slots it has just read with the rows kRing further on.  Row x sits in slot
+    // (x - ra) mod kRing.
     const bool ring_on = wrows && nf > 0;
-    const float* isrc = ring_on ? grow0 + 3LL * ra * it.nv + (al16 ? 4 * lane : lane) : nullptr;
-    float* idst = ring + (al16 ? 4 * lane : lane);
+    const int ioff = al16 ? 4 * lane : lane;
+    const float* isrc = ring_on ? grow0 + 3LL * ra * it.nv + ioff : nullptr;
     const bool il16 = al16 && lane * 4 < nf;
-    auto issue = [&](int r) {
-        if (ring_on && r < rb) {
+    auto issue_row = [&](int x) {
+        if (ring_on && x < rb) {
+            float* d = ring + ((x - ra) & (kRing - 1)) * 96 + ioff;
             if (al16) {
-                if (il16) cp_async16(idst, isrc);
+                if (il16) cp_async16(d, isrc);
             } else {
-                for (int k = 0; lane + k < nf; k += 32) cp_async4(idst + k, isrc + k);
+                for (int k = 0; lane + k < nf; k += 32) cp_async4(d + k, isrc + k);
             }
         }
         cp_async_commit();
         isrc += 3 * it.nv;
-        idst = ((r - ra) & (kRing - 1)) == kRing - 1 ? idst - (kRing - 1) * 96 : idst + 96;
     };
-    int nexti = ra;   // next row of the ring to request
     if constexpr (GRAD) {
 #pragma unroll
-        for (int d = 0; d < kRing - 1; ++d) issue(nexti++);
+        for (int d = 0; d < kRing; ++d) issue_row(ra + d);
     }
     __syncthreads();
 
@@ -502,7 +500,7 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
         for (int c = tid; c < ncols; c += bs) cp_async4(s_v + c, kp.params + it.param_v + tl.col0 + c);
     }
     // the whole control net rides along when it fits (else the tile's window follows
-    // later); it stays Cartesian (x, y, z, w), which the final pass also reads
+    // later); once landed it is kept as homogeneous points Pw = (w x, w y, w z, w)
     float4* s_win = reinterpret_cast<float4*>(smem + kp.off_win);
     const int ncp = it.n1 * it.m1;
     const bool net_staged = !empty && ncp <= kWinCap;
@@ -522,6 +520,12 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
     const float ulo = (P > 0) ? s_knU[P] : 0.f, uhi = (P > 0) ? s_knU[n + 1] : 0.f;
     const float vlo = s_knV[Q], vhi = s_knV[m + 1];
     const int npro_r = empty ? 0 : nrows, npro_c = empty ? 0 : ncols;   // empty tiles skip the tables
+    if (net_staged)
+        for (int e = tid; e < ncp; e += bs) s_win[e] = homog(s_win[e]);
+    if (GRAD && it.smemA) {   // the shared adjoint block of a single-tile item starts at zero
+        float4* sB = reinterpret_cast<float4*>(smem + kp.off_sa);
+        for (int e = tid; e < ncp; e += bs) sB[e] = f4zero();
+    }
     if (!empty) {
         unsigned e = 0;
         if (tl.tidx == 0) {
@@ -675,6 +679,10 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
     }
     if (win_only) cp_async_wait<0>();
     __syncthreads();
+    if (win_only) {
+        for (int e = tid; e < rw_t * cw_t; e += bs) s_win[e] = homog(s_win[e]);
+        __syncthreads();
+    }
 
     if (uactive) {
         const int svb = s_sv[blc];
@@ -691,43 +699,28 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
         const int m1 = it.m1;
 
         const float4* wbase = s_win + (svb - Q - w_j0) - iwl * w_stride;   // window element (i, column of h = 0)
-        auto computeQ = [&](int i) -> float4 {
-            // Qw = sum_h Nv_h (w x, w y, w z, w) of row i's Q+1 control points
+        // sum_h c_h Pw[i][column of h] over row i's Q+1 homogeneous control points: the
+        // staged window, else global memory (one branch per row, not per point: a
+        // per-point select costs the row loop its registers)
+        auto contract_row = [&](int i, const float (&c)[QB]) -> float4 {
             float4 acc = f4zero();
-            auto add = [&](float nv, float4 c) {
-                const float wn = nv * c.w;
-                acc.x = fmaf(wn, c.x, acc.x);
-                acc.y = fmaf(wn, c.y, acc.y);
-                acc.z = fmaf(wn, c.z, acc.z);
-                acc.w += wn;
-            };
             if (win) {
                 const float4* wr_ = wbase + i * w_stride;
 #pragma unroll
-                for (int h = 0; h < QB; ++h) add(Nv[h], wr_[h]);
+                for (int h = 0; h < QB; ++h) acc = fma4(c[h], wr_[h], acc);
             } else {
                 const float4* cr = cbase + i * m1;
 #pragma unroll
-                for (int h = 0; h < QB; ++h) add(Nv[h], __ldg(cr + h));
+                for (int h = 0; h < QB; ++h) acc = fma4(c[h], homog(__ldg(cr + h)), acc);
             }
             return acc;
         };
-
-        // tangents: Qv = sum_h dNv_h (w x, w y, w z, w) of row i's Q+1 control points
+        // Qw = sum_h Nv_h Pw of row i's Q+1 control points
+        auto computeQ = [&](int i) -> float4 { return contract_row(i, Nv); };
+        // tangents: Qv = sum_h dNv_h Pw of row i's Q+1 control points
         auto computeQv = [&](int i) -> float4 {
-            float4 acc = f4zero();
-            if constexpr (DER) {
-#pragma unroll
-                for (int h = 0; h < QB; ++h) {
-                    const float4 c = win ? (wbase + i * w_stride)[h] : __ldg(cbase + i * m1 + h);
-                    const float wn = dNv[h] * c.w;
-                    acc.x = fmaf(wn, c.x, acc.x);
-                    acc.y = fmaf(wn, c.y, acc.y);
-                    acc.z = fmaf(wn, c.z, acc.z);
-                    acc.w += wn;
-                }
-            }
-            return acc;
+            if constexpr (DER) return contract_row(i, dNv);
+            return f4zero();
         };
 
         // Retired control rows (consecutive, from ilo) wait in tbuf until kBatch of
@@ -744,35 +737,55 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
         float4* sOv = sA + (it.n1 + wr * PB) * it.m1;
         float4* uA = GRAD ? reinterpret_cast<float4*>(uslot + it.abase) : nullptr;
         int nb = 0, nst = 0, ilo = -1;
+        // One contraction task: batched row k, control column jj (sample range r2, weights w).
+        // Even and odd terms go to two accumulators, added at the end.
+        auto contract = [&](int k, int2 r2, const float* w) -> float4 {
+            const float4* tb = tbuf + k * uthreads + r2.x;
+            float4 a0 = f4zero(), a1 = f4zero();
+            int q = 0;
+            for (; q + 3 < r2.y; q += 4) {
+                a0 = fma4(w[q], tb[q], a0);
+                a1 = fma4(w[q + 1], tb[q + 1], a1);
+                a0 = fma4(w[q + 2], tb[q + 2], a0);
+                a1 = fma4(w[q + 3], tb[q + 3], a1);
+            }
+            if (q + 1 < r2.y) {
+                a0 = fma4(w[q], tb[q], a0);
+                a1 = fma4(w[q + 1], tb[q + 1], a1);
+                q += 2;
+            }
+            if (q < r2.y) a0 = fma4(w[q], tb[q], a0);
+            return make_float4(a0.x + a1.x, a0.y + a1.y, a0.z + a1.z, a0.w + a1.w);
+        };
+        auto put = [&](int k, int jj, float4 acc) {
+            const int gi = ilo + nst + k;
+            if (!sa) uA[(nst + k) * m1 + jj] = acc;
+            else if (gi <= pm) sOv[(gi - ilo) * m1 + jj] = acc;
+            else sA[gi * m1 + jj] = acc;
+        };
+        // When a full batch has a thread per task (cw_t * kBatch <= uthreads), thread ut
+        // takes task (ut / cw_t, ut % cw_t), without the general loop.
         auto flush = [&]() {
             unit_barrier(1 + wr, uthreads);
-            const int tasks = nb * cw_t;
-            for (int task = ut; task < tasks; task += uthreads) {
-                const int k = task / cw_t, jj = task - k * cw_t;
-                float4 acc;
-                if (jj < kJbCap) {
-                    const int2 r2 = s_jb[jj];
-                    const float* w = s_w + s_joff[jj];
-                    const float4* tb = tbuf + k * uthreads + r2.x;
-                    float4 a0 = f4zero(), a1 = f4zero();
-                    int q = 0;
-                    for (; q + 1 < r2.y; q += 2) {
-                        a0 = fma4(w[q], tb[q], a0);
-                        a1 = fma4(w[q + 1], tb[q + 1], a1);
+            if (cw_t * kBatch <= uthreads && cw_t <= kJbCap) {
+                const int k = ut / cw_t, jj = ut - k * cw_t;
+                if (k < nb) put(k, jj, contract(k, s_jb[jj], s_w + s_joff[jj]));
+            } else {
+                const int tasks = nb * cw_t;
+                for (int task = ut; task < tasks; task += uthreads) {
+                    const int k = task / cw_t, jj = task - k * cw_t;
+                    float4 acc;
+                    if (jj < kJbCap) {
+                        acc = contract(k, s_jb[jj], s_w + s_joff[jj]);
+                    } else {
+                        const int j = jlo_t + jj;
+                        const int lo = lower_bound_i(s_sv, ncols, j), hi = lower_bound_i(s_sv, ncols, j + Q + 1);
+                        const float4* tb = tbuf + k * uthreads;
+                        acc = f4zero();
+                        for (int b = lo; b < hi; ++b) acc = fma4(s_nv[b * SV + (j - s_sv[b] + Q)], tb[b], acc);
                     }
-                    if (q < r2.y) a0 = fma4(w[q], tb[q], a0);
-                    acc = make_float4(a0.x + a1.x, a0.y + a1.y, a0.z + a1.z, a0.w + a1.w);
-                } else {
-                    const int j = jlo_t + jj;
-                    const int lo = lower_bound_i(s_sv, ncols, j), hi = lower_bound_i(s_sv, ncols, j + Q + 1);
-                    const float4* tb = tbuf + k * uthreads;
-                    acc = f4zero();
-                    for (int b = lo; b < hi; ++b) acc = fma4(s_nv[b * SV + (j - s_sv[b] + Q)], tb[b], acc);
+                    put(k, jj, acc);
                 }
-                const int gi = ilo + nst + k;
-                if (!sa) uA[(nst + k) * m1 + jj] = acc;
-                else if (gi <= pm) sOv[(gi - ilo) * m1 + jj] = acc;
-                else sA[gi * m1 + jj] = acc;
             }
             nst += nb;
             nb = 0;
@@ -785,7 +798,7 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
                 if (win) {
                     const float4* wr_ = wbase + i * w_stride;
 #pragma unroll
-                    for (int h = 0; h < QB; ++h) Gam[h] += dot4(tv, homog(wr_[h]));
+                    for (int h = 0; h < QB; ++h) Gam[h] += dot4(tv, wr_[h]);
                 } else {
                     const float4* cr = cbase + i * m1;
 #pragma unroll
@@ -848,9 +861,6 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
         // NR = rows in the step; the ring slots of rows < r are free for refills.
         auto step = [&](auto nr_tag, int r) {
             constexpr int NR = decltype(nr_tag)::value;
-            if constexpr (GRAD) {
-                while (nexti <= r + kRing - 1) issue(nexti++);
-            }
             float Nu[NR][PB];
 #pragma unroll
             for (int q = 0; q < NR; ++q) load_basis<PB>(s_nu + (r + q) * SU, Nu[q]);
@@ -934,7 +944,9 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
                     const float gbx = gx * ginv, gby = gy * ginv, gbz = gz * ginv;
                     lam[q] = make_float4(gbx, gby, gbz, -fmaf(Sx[q], gbx, fmaf(Sy[q], gby, Sz[q] * gbz)));
                 }
-                __syncwarp();   // these slots are refilled by later requests
+                __syncwarp();   // every lane has read these slots: refill them kRing rows on
+#pragma unroll
+                for (int q = 0; q < NR; ++q) issue_row(r + q + kRing);
 #pragma unroll
                 for (int q = 0; q < NR; ++q)
 #pragma unroll
@@ -1126,7 +1138,7 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
         if (single) {
             // the only tile of its item: reduce its own units (shared memory or its slot)
             __syncthreads();
-            if (it.smemA) final_ctrl_smem(kp, it, nwr, PB, s_flag + 32, jlo_t, cw_t, net_staged ? s_win : nullptr);
+            if (it.smemA) final_ctrl_smem(kp, it, nwr, PB, s_flag + 32, jlo_t, cw_t);
             else final_reduce(kp, tl.item, true);
         } else {
             // publish the partials (the barrier orders the CTA's writes before thread 0's
