@@ -546,6 +546,7 @@ def bench_ragged(dev, steps, warmup, flush, peak, count=1000):
             "per_surface_launches": {"value": pk.npts / (ms_per / 1e3), "ms_per_step": ms_per},
             "speedup_vs_per_surface": ms_per / ms,
             "tiles": {f"p{g['key'][0]}q{g['key'][1]}": list(g["tile"]) for g in eng.groups},
+            "step_candidates_ms": {k: round(v, 4) for k, v in eng.step_candidates.items()},
             "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
                          "algorithmic_bytes": abytes}}
 

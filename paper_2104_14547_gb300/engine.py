@@ -21,8 +21,15 @@ import torch
 from . import _lib, batch, tune
 
 
+# uniform tile shapes the engine also times as whole steps (all groups side by side)
+DEFAULT_STEP_TILES = [(8, 128), (8, 64), (4, 128)]
+
+
 class RaggedEngine:
-    """tile: one (warps, rows) for every group instead of the per-group autotuner.
+    """tile: one (warps, rows) for every group instead of the autotuner.
+    With the autotuner, each group's shape is first tuned alone; the whole step is
+    then timed (as one CUDA graph) with those shapes and with each uniform shape of
+    step_candidates (default DEFAULT_STEP_TILES), and the fastest set is kept.
     budget: how a group's CTA cap is sized -- "warps" (its work share of a wave of
     16 warps per SM, what a 128-register tile kernel holds), "occupancy" (its
     share of the CTAs its kernel really fits per SM, nurbs_plan_occupancy) or
@@ -30,7 +37,7 @@ class RaggedEngine:
     served)."""
 
     def __init__(self, surfaces, targets_pts: np.ndarray, device="cuda", autotune=True, knots_grad=True,
-                 candidates=None, tile=None, budget="none"):
+                 candidates=None, tile=None, budget="none", step_candidates=None):
         self.device = torch.device(device)
         if self.device.index is None:
             self.device = torch.device("cuda", torch.cuda.current_device())
@@ -54,7 +61,8 @@ class RaggedEngine:
         for d in pk.descs:
             work[(int(d["p"]), int(d["q"]))] += int(d["nu"]) * int(d["nv"]) + 1
         total = sum(work.values())
-        self.groups = []
+        self._cap_fns = {}
+        tuned = {}
         for k in keys:
             sel = np.nonzero((pk.descs["p"] == k[0]) & (pk.descs["q"] == k[1]))[0]
             sub = pk.descs[sel]
@@ -68,19 +76,79 @@ class RaggedEngine:
                 per_sm = max(1, 16 // plan.warps) if budget == "warps" else max(1, plan.occupancy(op)[0])
                 return max(per_sm, int(round(share * sms * per_sm)))
 
+            self._cap_fns[k] = cap
             warps, rows = tile if tile is not None else (8, 128)
             if autotune and tile is None:
                 sub_packed = batch.Packed(pk.kind, sub, pk.knots, pk.ctrl, pk.params, pk.npts)
                 (warps, rows), _ = tune.autotune(sub_packed, self._tensors(), op="mse", candidates=candidates,
                                                  reps=3, device=self.device, max_ctas=cap,
                                                  budget_key=(budget, round(share, 6), sms))
-            max_ctas = cap(batch.Plan(pk.kind, sub, device=self.device, warps=warps, rows=rows))
+            tuned[k] = (warps, rows)
+        self.groups = self._build(keys, tuned)
+        self.step_candidates = {}
+        if autotune and tile is None:
+            # Each group was tuned alone, but the groups run side by side: time the whole
+            # step (one captured graph) for the per-group choice and for uniform tile
+            # shapes, and keep the fastest.
+            options = {"per_group": tuned}
+            for t in step_candidates or DEFAULT_STEP_TILES:
+                options[f"w{t[0]}r{t[1]}"] = {k: tuple(t) for k in keys}
+            best, best_ms = None, None
+            for name, tiles in options.items():
+                try:   # a shape whose tiles a kernel cannot hold is skipped
+                    groups = self._build(keys, tiles) if name != "per_group" else self.groups
+                    ms = self._time_graph(groups)
+                except _lib.NurbsError as e:
+                    if e.status != _lib.ERR_SIZE:
+                        raise
+                    continue
+                self.step_candidates[name] = ms
+                if best_ms is None or ms < best_ms:
+                    best, best_ms = groups, ms
+            self.groups = best
+        self.graph = None
+
+    def _build(self, keys, tiles):
+        """One plan per degree group with the given {key: (warps, rows)} tile shapes."""
+        pk = self.packed
+        groups = []
+        for k in keys:
+            sel = np.nonzero((pk.descs["p"] == k[0]) & (pk.descs["q"] == k[1]))[0]
+            sub = pk.descs[sel]
+            warps, rows = tiles[k]
+            max_ctas = self._cap_fns[k](batch.Plan(pk.kind, sub, device=self.device, warps=warps, rows=rows))
             plan = batch.Plan(pk.kind, sub, device=self.device, warps=warps, rows=rows, max_ctas=max_ctas)
             # loss_items is indexed by the plan's own item order: one buffer per group
-            self.groups.append(dict(key=k, items=sel, plan=plan, tile=(warps, rows), max_ctas=max_ctas,
-                                    loss=torch.zeros(len(sel), device=self.device),
-                                    stream=torch.cuda.Stream(self.device)))
-        self.graph = None
+            groups.append(dict(key=k, items=sel, plan=plan, tile=(warps, rows), max_ctas=max_ctas,
+                               loss=torch.zeros(len(sel), device=self.device),
+                               stream=torch.cuda.Stream(self.device)))
+        return groups
+
+    def _time_graph(self, groups, reps: int = 3) -> float:
+        """Median ms of the whole step for a set of group plans, captured in a graph
+        and replayed with L2 flushed before each replay."""
+        saved = self.groups
+        self.groups = groups
+        try:
+            self.step()                               # first launch outside the capture
+            torch.cuda.synchronize(self.device)
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g):
+                self.step()
+            flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=self.device)
+            ts = []
+            for _ in range(reps + 1):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                g.replay()
+                e1.record()
+                e1.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            del g, flush
+            return float(np.median(ts[1:]))
+        finally:
+            self.groups = saved
 
     def _tensors(self):
         return dict(knots=self.knots, ctrl=self.ctrl, params=self.params, target=self.target, pts=self.pts,

@@ -107,6 +107,7 @@ class Request:
     result: object = None
     error: str | None = None  # set when the server failed (or cancelled) the request
     payload: object = None    # "restore": the checkpoint to put back
+    out: np.ndarray | None = None   # "eval": float32 array of the model's nu*nv*3 floats to fill (else allocated)
     cancelled: bool = False
     done: threading.Event = field(default_factory=threading.Event)
 
@@ -146,6 +147,10 @@ class Server:
         self.alloc_pts = RangeAllocator(self.n_pts)
         self.alloc_scalar = RangeAllocator(self.n_scalar)
         self.models: dict[int, Model] = {}
+        # the models' descriptor fields as one int64 table (row = model id), for building a
+        # wave's descriptors with array operations: p q n1 m1 nu nv knot_u knot_v ctrl
+        # param_u param_v target steps
+        self._mt = np.zeros((0, 13), np.int64)
         self.max_wave = max_wave
         self.out_points = out_points
         self.lr = lr
@@ -190,6 +195,9 @@ class Server:
         mid = len(self.models)
         self.models[mid] = Model(mid, s.p, s.q, n1, m1, len(s.u), len(s.v), k, k + len(s.U), c,
                                  k + nk, k + nk + len(s.u), t)
+        row = np.array([[s.p, s.q, n1, m1, len(s.u), len(s.v), k, k + len(s.U), c, k + nk, k + nk + len(s.u), t, 0]],
+                       np.int64)
+        self._mt = np.concatenate([self._mt, row])
         return mid
 
     # ------------------------------------------------------------ requests
@@ -254,14 +262,20 @@ class Server:
         r.done.set()
 
     def _descs(self, entries, fit: bool):
+        mids = np.fromiter(((e if fit else e[0]).model for e in entries), np.int64, len(entries))
+        t = self._mt[mids]
         d = np.zeros(len(entries), batch.DESC_DTYPE)
-        for k, e in enumerate(entries):
-            r, off = (e, None) if fit else e
-            m = self.models[r.model]
+        for k, name in enumerate(("p", "q", "n1", "m1", "nu", "nv")):
+            d[name] = t[:, k]
+        for k, name in enumerate(("knot_u", "knot_v", "ctrl", "param_u", "param_v"), start=6):
+            d[name] = t[:, k]
+        if fit:
+            d["adam_step"] = t[:, 12] + 1
             # a fit item's loss is the mean over its own points: grad_scale 2 / (3 nu nv)
-            gs = np.float32(2.0 / (3.0 * max(m.nu * m.nv, 1))) if fit else 0.0
-            d[k] = (m.p, m.q, m.n1, m.m1, m.nu, m.nv, (m.steps + 1) if fit else 0, gs,
-                    m.knot_u, m.knot_v, m.ctrl, m.param_u, m.param_v, m.target if fit else off)
+            d["grad_scale"] = (2.0 / (3.0 * np.maximum(t[:, 4] * t[:, 5], 1))).astype(np.float32)
+            d["pts"] = t[:, 11]
+        else:
+            d["pts"] = np.fromiter((off for _, off in entries), np.int64, len(entries))
         return d
 
     def _plan(self, slot, kind, descs):
@@ -310,16 +324,22 @@ class Server:
         for e in w["events"]:
             e.synchronize()
         now = time.perf_counter()
-        ho = self.host_out[w["slot"]]
+        ho = self.host_out[w["slot"]].numpy()
         for r, off in w["evals"]:
             m = self.models[r.model]
             n = m.nu * m.nv
-            r.result = ho[off: off + n].numpy().reshape(m.nu, m.nv, 3).copy()
+            src = ho[off: off + n]
+            if r.out is not None:        # the caller's own buffer: no allocation here
+                np.copyto(r.out.reshape(-1, 3)[:n], src)
+                r.result = r.out
+            else:
+                r.result = src.reshape(m.nu, m.nv, 3).copy()
             self.points_done += n
-        hl = self.host_loss[w["slot"]]
+        hl = self.host_loss[w["slot"]].numpy()
         for k, r in enumerate(w["fits"]):
             m = self.models[r.model]
             m.steps += 1
+            self._mt[r.model, 12] = m.steps
             r.result = float(hl[k]) / (3.0 * m.nu * m.nv)
             self.points_done += m.nu * m.nv
         for r, _ in w["evals"]:
@@ -368,6 +388,7 @@ class Server:
             self.adam_m[m.ctrl: m.ctrl + n] = st["adam_m"].to(self.device)
             self.adam_v[m.ctrl: m.ctrl + n] = st["adam_v"].to(self.device)
             m.steps = int(st["steps"])
+            self._mt[mid, 12] = m.steps
         torch.cuda.synchronize(self.device)
 
     def checkpoint(self, timeout: float = 60.0) -> dict:
@@ -430,25 +451,42 @@ class Server:
 
 def poisson_run(server: Server, model_ids, n_requests: int, rate: float, eval_frac: float = 0.7, seed: int = 0):
     """Submit n_requests with exponential inter-arrival times at `rate` per second;
-    returns (latencies in seconds, wall seconds, points processed)."""
+    returns (latencies in seconds, wall seconds, points processed, requests).
+
+    A load generator, not a client that keeps results: every evaluation of a model
+    fills that model's one output array (overwritten by its later evaluations), and
+    Python's cyclic garbage collector is paused during the run, so that host-side
+    allocation and collection pauses do not show up as serving latency."""
+    import gc
+
     rng = np.random.default_rng(seed)
     gaps = rng.exponential(1.0 / rate, size=n_requests)
     kinds = rng.random(n_requests) < eval_frac
     mids = rng.choice(model_ids, size=n_requests)
+    outs = {int(m): np.empty(server.models[int(m)].nu * server.models[int(m)].nv * 3, np.float32)
+            for m in set(mids.tolist())}
     reqs = []
-    p0 = server.points_done
-    t0 = time.perf_counter()
-    t_next = t0
-    for k in range(n_requests):
-        t_next += gaps[k]
-        while True:
-            dt = t_next - time.perf_counter()
-            if dt <= 0:
-                break
-            time.sleep(min(dt, 0.001) if dt > 2e-4 else 0)
-        reqs.append(server.submit(Request("eval" if kinds[k] else "fit", int(mids[k]))))
-    for r in reqs:
-        if not r.done.wait(timeout=120.0) or r.error is not None:
-            raise RuntimeError(f"request not served: {r.error or 'timeout'}")
-    wall = time.perf_counter() - t0
+    gc_was = gc.isenabled()
+    gc.collect()
+    gc.disable()
+    try:
+        p0 = server.points_done
+        t0 = time.perf_counter()
+        t_next = t0
+        for k in range(n_requests):
+            t_next += gaps[k]
+            while True:
+                dt = t_next - time.perf_counter()
+                if dt <= 0:
+                    break
+                time.sleep(min(dt, 0.001) if dt > 2e-4 else 0)
+            m = int(mids[k])
+            reqs.append(server.submit(Request("eval", m, out=outs[m]) if kinds[k] else Request("fit", m)))
+        for r in reqs:
+            if not r.done.wait(timeout=120.0) or r.error is not None:
+                raise RuntimeError(f"request not served: {r.error or 'timeout'}")
+        wall = time.perf_counter() - t0
+    finally:
+        if gc_was:
+            gc.enable()
     return np.array([r.latency for r in reqs]), wall, server.points_done - p0, reqs

@@ -313,3 +313,21 @@ def test_server_admission_refuses_when_arena_is_full():
     admitted = [m for m in got if m is not None]
     assert 0 < len(admitted) < len(got)
     assert all(m is None for m in got[len(admitted):])   # once full, every later model is refused
+
+
+def test_server_eval_into_caller_buffer():
+    # an evaluation with a caller-provided output array fills it with the same bits
+    srv = serve.Server(hbm_fraction=0.02, max_wave=64, out_points=1 << 20)
+    mids, surfs, _ = _server_models(srv, 50, 3)
+    srv.start()
+    try:
+        for m, s in zip(mids, surfs):
+            a = srv.submit(serve.Request("eval", m))
+            _wait(a)
+            buf = np.full(s.npts * 3, np.nan, np.float32)
+            b = srv.submit(serve.Request("eval", m, out=buf))
+            _wait(b)
+            assert b.result is buf
+            assert np.array_equal(buf.reshape(a.result.shape), a.result)
+    finally:
+        srv.stop()
