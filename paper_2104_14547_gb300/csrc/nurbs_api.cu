@@ -61,6 +61,8 @@ struct nurbs_plan {
     int smem_der;             // forward with tangents (derivative tables where the adjoint would be)
     int c_mc, c_wbytes, c_smem;   // curve kernels: control capacity, bytes per warp, per CTA
     int c_wbytes_f, c_smem_f;     // the same for the forward-only curve kernels
+    int ring_rows;                // rows of dL/dS (or target) in flight per warp (8 or 4)
+    int win_cap;                  // largest control net staged in shared memory (0: none)
     float knot_sigma;             // smoothed-indicator knot derivative bandwidth (0: off)
     int grad_homog;               // control-point gradients with respect to Pw
     // workspace layout (bytes)
@@ -243,9 +245,7 @@ nurbs_status nurbs_plan_create(int32_t kind, const nurbs_desc* h_desc, int32_t c
                     maxC = std::max(maxC, nwc * 32);
                 }
             }
-            it.ntiles = ntl;
-            // single-tile items keep their adjoint in shared memory when it fits
-            it.smemA = (ntl == 1 && smem_adjoint_bytes(it, nwr) <= (size_t)kSmemACap) ? 1 : 0;
+            it.ntiles = ntl;   // single-tile items keep their adjoint in shared memory when it fits (carve)
         }
         grp.t1 = (int)pl->tiles.size();
         if (grp.t1 > grp.t0) pl->groups.push_back(grp);
@@ -259,11 +259,6 @@ nurbs_status nurbs_plan_create(int32_t kind, const nurbs_desc* h_desc, int32_t c
     }
     pl->R = maxR;
     pl->C = maxC;
-    size_t off = 0;
-    auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 16); return (int)o; };
-    pl->off_misc = take(256);
-    pl->off_su = take(4 * maxR);
-    pl->off_u = take(4 * maxR);
     // per-degree table strides (the kernels' SU, SV, KU, KV)
     int su = 4, sv = 4, ku = 1, kv = 2;
     for (const ItemDev& it : pl->items) {
@@ -272,43 +267,76 @@ nurbs_status nurbs_plan_create(int32_t kind, const nurbs_desc* h_desc, int32_t c
         ku = std::max(ku, 2 * it.p);
         kv = std::max(kv, 2 * it.q);
     }
-    pl->off_nu = take(4 * maxR * su);
-    pl->off_sv = take(4 * maxC);
-    pl->off_v = take(4 * maxC);
-    pl->off_nv = take(4 * maxC * sv);
-    pl->off_stage = take(16 * kBatch * max_unit_cols);
-    pl->off_beta = take(4 * max_nwc * maxR * su);
-    pl->off_duc = take(4 * maxR * ku);
-    pl->off_dvc = take(4 * max_nwr * maxC * kv);
-    pl->off_ring = take(4 * NW * kRing * 96);   // only the grad kernels use it
-    pl->off_jb = take(8 * kJbCap);
-    pl->off_win = take(16 * kWinCap);
-    pl->off_run = take(4 * maxR);
     int max_knots = 4;
     for (const ItemDev& it : pl->items)
         max_knots = std::max(max_knots, align4(it.n1 + it.p + 1) + it.m1 + it.q + 1);
-    pl->off_knots = take(4 * max_knots);
-    pl->off_w = take(4 * (kJbCap + maxC * sv));
-    size_t sa_bytes = 0;
-    for (const ItemDev& it : pl->items)
-        if (it.smemA) sa_bytes = std::max(sa_bytes, smem_adjoint_bytes(it, pl->tiles[it.first_tile].nwr));
-    pl->smem_eval = (int)off;     // the forward kernels stop here
-    // the row basis derivatives of the forward with tangents take the place of the
-    // shared adjoint, which only the gradient kernels use
-    pl->off_dnu = (int)off;
-    pl->smem_der = (int)align_up(off + 4 * (size_t)maxR * su, 16);
-    pl->off_sa = take(sa_bytes);
-    pl->off_acc = pl->off_su;     // the final reduction reuses the tile tables
     int max_units = 1;
     for (const ItemDev& it : pl->items) {
         int u = 0;
         for (int t = it.first_tile; t < it.first_tile + it.ntiles; ++t) u += pl->tiles[t].nwr;
         max_units = std::max(max_units, u);
     }
-    const size_t min_acc = std::max<size_t>(16 * 1024, 32 * (size_t)max_units);
-    if (off < (size_t)pl->off_acc + min_acc) off = pl->off_acc + min_acc;
-    pl->acc_cap = (int)(off - pl->off_acc);
-    pl->smem_bytes = (int)off;
+    // Shared memory carve-up for the largest tile, given the rows of dL/dS (or target)
+    // in flight per warp, the largest staged control net and the largest shared adjoint
+    // (single-tile items whose adjoint exceeds it use the workspace instead).
+    auto carve = [&](int ring_rows, int win_cap, size_t sa_cap) {
+        for (ItemDev& it : pl->items)
+            it.smemA = (!it.ck && it.ntiles == 1 &&
+                        smem_adjoint_bytes(it, pl->tiles[it.first_tile].nwr) <= sa_cap) ? 1 : 0;
+        pl->ring_rows = ring_rows;
+        pl->win_cap = win_cap;
+        size_t off = 0;
+        auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 16); return (int)o; };
+        pl->off_misc = take(256);
+        pl->off_su = take(4 * maxR);
+        pl->off_u = take(4 * maxR);
+        pl->off_nu = take(4 * maxR * su);
+        pl->off_sv = take(4 * maxC);
+        pl->off_v = take(4 * maxC);
+        pl->off_nv = take(4 * maxC * sv);
+        pl->off_stage = take(16 * kBatch * max_unit_cols);
+        pl->off_beta = take(4 * max_nwc * maxR * su);
+        pl->off_duc = take(4 * maxR * ku);
+        // column cotangents: one row of kv per (row group, column) of a tile; a tile has at
+        // most as many (row group, column) pairs as its warps have lanes
+        pl->off_dvc = take(4 * (size_t)max_unit_cols * kv);
+        pl->off_ring = take(4 * NW * ring_rows * 96);   // only the grad kernels use it
+        pl->off_jb = take(8 * kJbCap);
+        pl->off_win = take(16 * (size_t)win_cap);
+        pl->off_run = take(4 * maxR);
+        pl->off_knots = take(4 * max_knots);
+        pl->off_w = take(4 * (kJbCap + maxC * sv));
+        size_t sa_bytes = 0;
+        for (const ItemDev& it : pl->items)
+            if (it.smemA) sa_bytes = std::max(sa_bytes, smem_adjoint_bytes(it, pl->tiles[it.first_tile].nwr));
+        pl->smem_eval = (int)off;     // the forward kernels stop here
+        // the row basis derivatives of the forward with tangents take the place of the
+        // shared adjoint, which only the gradient kernels use
+        pl->off_dnu = (int)off;
+        pl->smem_der = (int)align_up(off + 4 * (size_t)maxR * su, 16);
+        pl->off_sa = take(sa_bytes);
+        pl->off_acc = pl->off_su;     // the final reduction reuses the tile tables
+        const size_t min_acc = std::max<size_t>(16 * 1024, 32 * (size_t)max_units);
+        if (off < (size_t)pl->off_acc + min_acc) off = pl->off_acc + min_acc;
+        pl->acc_cap = (int)(off - pl->off_acc);
+        pl->smem_bytes = (int)off;
+    };
+    carve(kRing, kWinCap, kSmemACap);
+    // A plan asked for k >= 2 persistent CTAs per SM gets a carve-up that lets k gradient
+    // CTAs share an SM (228 KB of shared memory per SM, 1 KB of it reserved per CTA):
+    // first half the rows in flight per warp, then a smaller shared adjoint, then no
+    // staged control net (the kernels then read control points from global memory).
+    if (pl->ctas_per_sm >= 2) {
+        const size_t budget = (size_t)kSmemPerSM / pl->ctas_per_sm - 1024;
+        auto fit_sa = [&](int ring_rows, int win_cap) {
+            carve(ring_rows, win_cap, 0);
+            const size_t rest = (size_t)pl->smem_bytes;
+            carve(ring_rows, win_cap, rest < budget ? std::min<size_t>(budget - rest, kSmemACap) : 0);
+        };
+        if ((size_t)pl->smem_bytes > budget) carve(kRing / 2, kWinCap, kSmemACap);
+        if ((size_t)pl->smem_bytes > budget) fit_sa(kRing / 2, kWinCap);
+        if ((size_t)pl->smem_bytes > budget) fit_sa(kRing / 2, 0);
+    }
     // workspace layout
     size_t w = kHeaderBytes;
     pl->items_off = w; w = align_up(w + sizeof(ItemDev) * pl->items.size(), 256);
@@ -452,6 +480,8 @@ void fill_tables(KParams& kp, const nurbs_plan* pl, unsigned char* ws)
     kp.c_mc = pl->c_mc;
     kp.c_wbytes = pl->c_wbytes;
     kp.knot_sigma = pl->knot_sigma;
+    kp.ring_rows = pl->ring_rows;
+    kp.win_cap = pl->win_cap;
     kp.grad_homog = pl->grad_homog;
 }
 

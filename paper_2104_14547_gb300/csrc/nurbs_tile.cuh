@@ -39,11 +39,12 @@ enum : unsigned {
     kErrOrder = 1u << 5,
 };
 
-constexpr int kRing = 8;        // rows of dL/dS (or target) in flight per warp (power of two)
+constexpr int kRing = 8;        // rows of dL/dS (or target) in flight per warp (the default; a plan may use kRing / 2)
 constexpr int kBatch = 4;       // retired control rows contracted together
 constexpr int kJbCap = 256;     // column ranges cached per tile
 constexpr int kWinCap = 1024;   // control points staged in shared memory (whole net, else the tile's window)
 constexpr int kSmemACap = 40 * 1024;   // bytes of shared adjoint per single-tile item
+constexpr int kSmemPerSM = 228 * 1024; // shared memory of one SM (sm_103)
 
 struct KParams {
     const ItemDev* items;
@@ -80,6 +81,8 @@ struct KParams {
     int c_mc, c_wbytes;      // curve kernels: control-point capacity, shared bytes per warp
     float knot_sigma;        // > 0: knot derivative with the Gaussian-smoothed indicator term
     int grad_homog;          // grad_ctrl receives dL/dPw (homogeneous) instead of dL/d(P, w)
+    int ring_rows;           // rows of dL/dS (or target) in flight per warp: kRing or kRing / 2
+    int win_cap;             // control points staged in shared memory at most (0: none)
 };
 
 __device__ __forceinline__ float4 f4zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
@@ -456,23 +459,24 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
 
     // ring of incoming dL/dS (or target) rows for this warp's columns; the first
     // rows are requested before the prologue so their latency overlaps it
-    float* ring = reinterpret_cast<float*>(smem + kp.off_ring) + warp * (kRing * 96);
+    const int nring = kp.ring_rows;   // a power of two
+    float* ring = reinterpret_cast<float*>(smem + kp.off_ring) + warp * (nring * 96);
     const int nf = 3 * nvw;
     const long long prow0 = it.pts + (long long)tl.row0 * it.nv + tl.col0 + wcol0;  // point (row 0, lane 0)
     const float* grow0 = GRAD ? kp.gin + 3 * prow0 : nullptr;
     const bool al16 = ((prow0 & 3) == 0) && ((it.nv & 3) == 0) && ((nvw & 3) == 0);
     const bool wrows = !empty && wr < nwr && ra < rb;
     // Requests go out in row order, one commit group per row (empty past the unit's
-    // rows): the first kRing rows before the prologue, then each step refills the
-    // slots it has just read with the rows kRing further on.  Row x sits in slot
-    // (x - ra) mod kRing.
+    // rows): the first nring rows before the prologue, then each step refills the
+    // slots it has just read with the rows nring further on.  Row x sits in slot
+    // (x - ra) mod nring.
     const bool ring_on = wrows && nf > 0;
     const int ioff = al16 ? 4 * lane : lane;
     const float* isrc = ring_on ? grow0 + 3LL * ra * it.nv + ioff : nullptr;
     const bool il16 = al16 && lane * 4 < nf;
     auto issue_row = [&](int x) {
         if (ring_on && x < rb) {
-            float* d = ring + ((x - ra) & (kRing - 1)) * 96 + ioff;
+            float* d = ring + ((x - ra) & (nring - 1)) * 96 + ioff;
             if (al16) {
                 if (il16) cp_async16(d, isrc);
             } else {
@@ -483,8 +487,7 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
         isrc += 3 * it.nv;
     };
     if constexpr (GRAD) {
-#pragma unroll
-        for (int d = 0; d < kRing; ++d) issue_row(ra + d);
+        for (int d = 0; d < nring; ++d) issue_row(ra + d);
     }
     __syncthreads();
 
@@ -503,7 +506,7 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
     // later); once landed it is kept as homogeneous points Pw = (w x, w y, w z, w)
     float4* s_win = reinterpret_cast<float4*>(smem + kp.off_win);
     const int ncp = it.n1 * it.m1;
-    const bool net_staged = !empty && ncp <= kWinCap;
+    const bool net_staged = !empty && ncp <= kp.win_cap;
     if (net_staged) {
         const float4* src = kp.ctrl + it.ctrl;
         for (int e = tid; e < ncp; e += bs)
@@ -654,7 +657,7 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
     // [jlo_t, jlo_t+cw_t), when it fits
     const int iwl = (bad || net_staged) ? 0 : s_su[0] - P;
     const int rw_t = bad ? 0 : s_su[nrows - 1] - (s_su[0] - P) + 1;
-    const bool win_only = !bad && !net_staged && rw_t * cw_t <= kWinCap;
+    const bool win_only = !bad && !net_staged && rw_t * cw_t <= kp.win_cap;
     const bool win = net_staged || win_only;
     const int w_j0 = net_staged ? 0 : jlo_t;        // window column of element 0
     const int w_stride = net_staged ? it.m1 : cw_t;  // window row stride
@@ -919,12 +922,17 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
                     }
                 }
             } else {
-                if constexpr (NR == 2) cp_async_wait<kRing - 2>(); else cp_async_wait<kRing - 1>();
+                // rows r .. r+nring-1 are in flight, one group each: wait for the first NR
+                if (nring == kRing) {
+                    if constexpr (NR == 2) cp_async_wait<kRing - 2>(); else cp_async_wait<kRing - 1>();
+                } else {
+                    if constexpr (NR == 2) cp_async_wait<kRing / 2 - 2>(); else cp_async_wait<kRing / 2 - 1>();
+                }
                 __syncwarp();
                 float4 lam[NR];
 #pragma unroll
                 for (int q = 0; q < NR; ++q) {
-                    const float* gp = ring + ((r + q - ra) & (kRing - 1)) * 96 + 3 * lane;
+                    const float* gp = ring + ((r + q - ra) & (nring - 1)) * 96 + 3 * lane;
                     float gx, gy, gz;
                     float ginv = inv[q];   // dL/dS = ginv * W * (gx, gy, gz)
                     if constexpr (MSE) {
@@ -944,9 +952,9 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
                     const float gbx = gx * ginv, gby = gy * ginv, gbz = gz * ginv;
                     lam[q] = make_float4(gbx, gby, gbz, -fmaf(Sx[q], gbx, fmaf(Sy[q], gby, Sz[q] * gbz)));
                 }
-                __syncwarp();   // every lane has read these slots: refill them kRing rows on
+                __syncwarp();   // every lane has read these slots: refill them nring rows on
 #pragma unroll
-                for (int q = 0; q < NR; ++q) issue_row(r + q + kRing);
+                for (int q = 0; q < NR; ++q) issue_row(r + q + nring);
 #pragma unroll
                 for (int q = 0; q < NR; ++q)
 #pragma unroll
@@ -997,7 +1005,7 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
                 // the column's Gamma of this unit; the knot derivative is linear in it, so
                 // the epilogue sums the units first and differentiates once per column
                 if (cvalid) {
-                    float* gv = reinterpret_cast<float*>(smem + kp.off_dvc) + (wr * kp.C + bl) * KV;
+                    float* gv = reinterpret_cast<float*>(smem + kp.off_dvc) + (wr * (nwc * 32) + bl) * KV;
 #pragma unroll
                     for (int h = 0; h < QB; ++h) gv[h] = Gam[h];
                 }
@@ -1073,7 +1081,7 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
                         for (int h = 0; h < QB; ++h) G[h] = 0.f;
                         for (int g = 0; g < ngv; ++g) {
 #pragma unroll
-                            for (int h = 0; h < QB; ++h) G[h] += s_dvc[(g * kp.C + c) * KV + h];
+                            for (int h = 0; h < QB; ++h) G[h] += s_dvc[(g * (nwc * 32) + c) * KV + h];
                         }
                         float dk[2 * Q + 1];
                         const float vc = fminf(fmaxf(s_v[c], vlo), vhi);

@@ -21,8 +21,9 @@ import torch
 from . import _lib, batch, tune
 
 
-# uniform tile shapes the engine also times as whole steps (all groups side by side)
-DEFAULT_STEP_TILES = [(8, 128), (8, 64), (4, 128)]
+# uniform tile shapes the engine also times as whole steps (all groups side by side):
+# (warps, rows) or (warps, rows, CTAs per SM the shared-memory carve-up is sized for)
+DEFAULT_STEP_TILES = [(8, 128), (8, 64), (4, 128), (8, 128, 2), (8, 64, 2)]
 
 
 class RaggedEngine:
@@ -92,7 +93,8 @@ class RaggedEngine:
             # shapes, and keep the fastest.
             options = {"per_group": tuned}
             for t in step_candidates or DEFAULT_STEP_TILES:
-                options[f"w{t[0]}r{t[1]}"] = {k: tuple(t) for k in keys}
+                name = f"w{t[0]}r{t[1]}" + (f"c{t[2]}" if len(t) > 2 else "")
+                options[name] = {k: tuple(t) for k in keys}
             best, best_ms = None, None
             for name, tiles in options.items():
                 try:   # a shape whose tiles a kernel cannot hold is skipped
@@ -115,11 +117,14 @@ class RaggedEngine:
         for k in keys:
             sel = np.nonzero((pk.descs["p"] == k[0]) & (pk.descs["q"] == k[1]))[0]
             sub = pk.descs[sel]
-            warps, rows = tiles[k]
-            max_ctas = self._cap_fns[k](batch.Plan(pk.kind, sub, device=self.device, warps=warps, rows=rows))
-            plan = batch.Plan(pk.kind, sub, device=self.device, warps=warps, rows=rows, max_ctas=max_ctas)
+            warps, rows = tiles[k][:2]
+            per_sm = tiles[k][2] if len(tiles[k]) > 2 else 0
+            max_ctas = self._cap_fns[k](batch.Plan(pk.kind, sub, device=self.device, warps=warps, rows=rows,
+                                                   ctas_per_sm=per_sm))
+            plan = batch.Plan(pk.kind, sub, device=self.device, warps=warps, rows=rows, max_ctas=max_ctas,
+                              ctas_per_sm=per_sm)
             # loss_items is indexed by the plan's own item order: one buffer per group
-            groups.append(dict(key=k, items=sel, plan=plan, tile=(warps, rows), max_ctas=max_ctas,
+            groups.append(dict(key=k, items=sel, plan=plan, tile=tuple(tiles[k]), max_ctas=max_ctas,
                                loss=torch.zeros(len(sel), device=self.device),
                                stream=torch.cuda.Stream(self.device)))
         return groups
@@ -208,7 +213,8 @@ class PerItemEngine:
         for g in eng.groups:
             for k in g["items"]:
                 tile[int(k)] = g["tile"]
-        self.plans = [batch.Plan(pk.kind, pk.descs[k: k + 1], device=eng.device, warps=tile[k][0], rows=tile[k][1])
+        self.plans = [batch.Plan(pk.kind, pk.descs[k: k + 1], device=eng.device, warps=tile[k][0], rows=tile[k][1],
+                                 ctas_per_sm=tile[k][2] if len(tile[k]) > 2 else 0)
                       for k in range(pk.count)]
 
     def step(self):

@@ -331,3 +331,37 @@ def test_server_eval_into_caller_buffer():
             assert np.array_equal(buf.reshape(a.result.shape), a.result)
     finally:
         srv.stop()
+
+
+def test_two_ctas_per_sm_carve_up_same_results():
+    # degree-5 items up to 256 samples wide need more shared memory than two 8-warp CTAs
+    # can share; a plan asked for 2 CTAs per SM trims its carve-up (fewer target rows in
+    # flight, adjoints through the workspace, no staged net) and gives the same results
+    surfs, tg = synth.ragged_batch(52, batch=10, deg=(5, 5), net=(30, 48), grid=(180, 256))
+    T = np.concatenate([O.surface_eval(t.p, t.q, t.U, t.V, t.ctrl, t.u, t.v).reshape(-1, 3) for t in tg])
+    pk = batch.pack_surfaces(surfs)
+    kn, ct, pr = batch.to_device(pk)
+    Td = torch.from_numpy(T.astype(np.float32)).cuda()
+    outs, occs = [], []
+    for per_sm in (0, 2):
+        plan = batch.Plan.for_packed(pk, warps=8, rows=128, ctas_per_sm=per_sm)
+        occs.append(plan.occupancy("mse_knots")[0])
+        pts, gc, gk = torch.empty_like(Td), torch.empty_like(ct), torch.empty_like(kn)
+        loss = torch.empty(pk.count, device="cuda")
+        plan.mse_fwd_bwd(kn, ct, pr, Td, pts, gc, gk, loss, 2.0 / (3 * pk.npts))
+        assert plan.get_error()[0] == 0
+        outs.append((pts, gc, gk, loss))
+    assert occs[0] == 1 and occs[1] == 2, occs
+    for a, b in zip(*outs):
+        assert torch.equal(a, b)
+    # and both agree with the oracle on a sample of items
+    S = batch.unpack_points(pk, outs[1][0].cpu().numpy())
+    dc = batch.unpack_ctrl(pk, outs[1][1].cpu().numpy())
+    Tk = batch.unpack_points(pk, T)
+    for k in (0, 5, 9):
+        s = surfs[k]
+        ref = O.surface_eval(s.p, s.q, s.U, s.V, s.ctrl, s.u, s.v)
+        assert np.abs(S[k] - ref).max() <= S_TOL * bbox_diag(s.ctrl)
+        _, g = O.mse(ref, Tk[k].astype(np.float64), 3 * pk.npts)
+        rc, _, _ = O.surface_vjp(s.p, s.q, s.U, s.V, s.ctrl, s.u, s.v, g)
+        assert rel_inf(dc[k], rc) <= G_TOL
