@@ -36,6 +36,12 @@ WORKLOAD = {"workload": "256 bicubic NURBS surfaces, 32x32 control nets, random 
 METRIC = "surface pts/s fwd+bwd FP32"
 
 
+def run_config(world: int) -> dict:
+    """The `config` object of both arms' lines: the workload, how L2 is kept cold
+    between timed steps on the GPU arm, and the replica count."""
+    return dict(WORKLOAD, l2_flush="256 MiB write before every timed GPU step", parallelism=f"replicas{world}")
+
+
 def algorithmic_bytes(npts: int, descs) -> int:
     """Bytes the method must move for one fwd+MSE+bwd step.
 
@@ -281,9 +287,9 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": "pts/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded, shapes of the paper's fitting workloads)",
-            "config": dict(WORKLOAD, l2_flush="256 MiB write before every timed step", parallelism=f"replicas{world}",
-                           points_per_step=npts * world, tile={"warps": best[0], "rows": best[1]},
-                           autotune_ms={f"w{w}r{r}": round(v, 4) for (w, r), v in table.items()}),
+            "config": run_config(world),
+            "run": {"points_per_step": npts * world, "tile": {"warps": best[0], "rows": best[1]},
+                    "autotune_ms": {f"w{w}r{r}": round(v, 4) for (w, r), v in table.items()}},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "algorithmic_bytes": abytes,
                          "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy)" if peaks else "fallback 6.8 TB/s",
@@ -582,6 +588,36 @@ def bench_serve(dev, rates=(1000, 2000, 5000, 10000, 20000, 50000), n_requests=2
             "sweep": out}
 
 
+def run_ragged_group(args):
+    """One degree group of the 1000-surface ragged workload, alone: two fused steps
+    with the given tile (for a single-kernel profile of a ragged group's kernel)."""
+    import torch
+    from paper_2104_14547_gb300 import batch, synth
+    p, q = (int(x) for x in args.ragged_group.split(","))
+    shape = [int(x) for x in (args.tile or "8,128").split(",")]
+    w, r, c = (shape + [0])[:3]
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    surfs, targets = synth.ragged_batch(0, 1000)
+    pk, tk = batch.pack_surfaces(surfs), batch.pack_surfaces(targets)
+    kn, ct, pr = batch.to_device(pk, dev)
+    _, tct, _ = batch.to_device(tk, dev)
+    T = torch.empty((pk.npts, 3), device=dev)
+    batch.Plan.for_packed(tk, device=dev).eval(kn, tct, pr, T)
+    sel = np.nonzero((pk.descs["p"] == p) & (pk.descs["q"] == q))[0]
+    plan = batch.Plan(pk.kind, pk.descs[sel], device=dev, warps=w, rows=r, ctas_per_sm=c)
+    pts, gc, gk = torch.empty_like(T), torch.empty_like(ct), torch.empty_like(kn)
+    loss = torch.empty(len(sel), device=dev)
+    for _ in range(2):
+        plan.mse_fwd_bwd(kn, ct, pr, T, pts, gc, gk, loss, 2.0 / (3 * pk.npts))
+    torch.cuda.synchronize(dev)
+    d = pk.descs[sel]
+    print(json.dumps({"ragged_group": [p, q], "items": int(len(sel)),
+                      "points": int((d["nu"].astype(np.int64) * d["nv"]).sum()), "tiles": plan.tiles,
+                      "ctas": plan.ctas, "occupancy": list(plan.occupancy("mse_knots")), "tile": [w, r, c],
+                      "error": list(plan.get_error())}))
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -616,7 +652,8 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded)", "impl": "reference",
-            "config": dict(WORKLOAD, sample_per_step=f"{per_step} surfaces"),
+            "config": run_config(int(os.environ.get("WORLD_SIZE", "1"))),
+            "run": {"sample_per_step": f"{per_step} surfaces, one thread per host core"},
             "cpu_baseline": {"value": value, "unit": "pts/s", "cores": cores, "kind": "oracle",
                              "sample": f"{per_step} of {WORKLOAD['batch']} surfaces per step, one thread per "
                                        f"host core"},
@@ -636,13 +673,18 @@ def main():
     ap.add_argument("--extras", default="curves,derivs,ragged,offset,chamfer,serve",
                     help="comma-separated extra workloads: curves, derivs, ragged, offset, chamfer, serve "
                          "(Poisson serving sweep, 6 rates)")
-    ap.add_argument("--tile", default="", help="fixed tile shape 'warps,rows' instead of the autotuner's")
+    ap.add_argument("--tile", default="", help="fixed tile shape 'warps,rows' instead of the autotuner's "
+                    "(with --ragged-group: 'warps,rows[,ctas_per_sm]')")
+    ap.add_argument("--ragged-group", default="", help="'p,q': run that degree group of the ragged workload "
+                    "alone, two fused steps (for profiling one group's kernel)")
     ap.add_argument("--serve", action="store_true", help="run the serving sweep even when --extras leaves it out")
     ap.add_argument("--serve-requests", type=int, default=20000, help="requests per arrival rate")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    if args.impl == "reference":
+    if args.ragged_group:
+        run_ragged_group(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)
