@@ -386,3 +386,28 @@ def _check_flag(items, status, kind=None):
     assert flags & (1 << status), (st, flags)
     # the workspace stays usable: a clean call afterwards reports nothing
     assert plan.get_error()[0] == 0
+
+
+def test_item_mean_loss_scale_matches_oracle():
+    # each item's own MSE normalisation (descriptor grad_scale = 2 / (3 x its points)):
+    # the call's grad_scale is ignored and every gradient matches the oracle's for that
+    # item's own mean, on the curve kernels, the tile path for long curves and surfaces
+    rng = np.random.default_rng(53)
+    curves = [synth.curve(rng, 3, 20, 300), synth.curve(rng, 4, 300, 700, knots="uniform"), synth.curve(rng, 2, 12, 50)]
+    surfs = [synth.surface(rng, 3, 3, 10, 10, 40, 30), synth.surface(rng, 2, 4, 8, 9, 25, 70)]
+    for items, kind in ((curves, CURVE), (surfs, SURF)):
+        pk = pack(items, kind)
+        plan = batch.Plan.for_packed(pk, item_mean=True)
+        kn, ct, pr = batch.to_device(pk)
+        T = rng.normal(size=(pk.npts, 3)).astype(np.float32)
+        gc = torch.zeros_like(ct)
+        loss = torch.zeros(pk.count, device="cuda")
+        plan.mse_fwd_bwd(kn, ct, pr, torch.from_numpy(T).cuda(), None, gc, None, loss, grad_scale=123.0)
+        assert plan.get_error()[0] == 0
+        dcs = batch.unpack_ctrl(pk, gc.cpu().numpy())
+        for k, (it, Tk) in enumerate(zip(items, batch.unpack_points(pk, T))):
+            S = oracle_eval(it, kind)
+            Tk = Tk.reshape(S.shape).astype(np.float64)
+            _, g = O.mse(S, Tk, 3 * Tk.reshape(-1, 3).shape[0])
+            dc = oracle_vjp(it, kind, g)[0]
+            assert rel_inf(dcs[k], dc) <= G_TOL, (kind, k)
