@@ -82,6 +82,35 @@ def test_curves_clustered_samples():
     _check_grads(items, CURVE, pk, g, gc, gk)
 
 
+def test_forward_curve_edge_cases():
+    # small curves (a small shared layout per warp) of every degree
+    rng = np.random.default_rng(46)
+    items = []
+    for p in (1, 2, 3, 4, 5):
+        c = synth.curve(rng, p, 20, 2, knots="uniform")
+        U = c.U.copy()
+        U[p + 3:2 * p + 3] = U[p + 3]   # an interior knot of multiplicity p: spans of zero length
+        u = np.sort(np.concatenate([np.linspace(0.0, 1.0, 61), U[p:20 + 1]]).astype(np.float32))   # samples on every knot
+        items.append(synth.Curve(p, U, c.ctrl, u))
+        # clustered samples: some lanes of a warp step pass the 32 staged knots
+        c2 = synth.curve(rng, p, 60, 2, knots="uniform")
+        u2 = np.concatenate([np.linspace(0.0, 0.02, 20), np.linspace(0.97, 1.0, 23)]).astype(np.float32)
+        items.append(synth.Curve(p, c2.U, c2.ctrl, np.sort(u2)))
+    # a single Bezier span (n = p), a one-sample curve and an empty one
+    items.append(synth.Curve(3, np.array([0, 0, 0, 0, 1, 1, 1, 1], np.float32),
+                             synth.random_walk_polygon(rng, 4), synth.uniform_params(33)))
+    items.append(synth.curve(rng, 2, 7, 1))
+    items.append(synth.curve(rng, 3, 12, 0))
+    _, got = gpu_eval(items, CURVE)
+    check_points(items, CURVE, got)
+    # clamped knots interpolate the end points
+    c = synth.Curve(3, synth.clamped_uniform_knots(10, 3), synth.random_walk_polygon(rng, 10),
+                    np.array([0.0, 1.0], np.float32))
+    _, g = gpu_eval([c], CURVE)
+    np.testing.assert_allclose(g[0][0], c.ctrl[0, :3], atol=1e-6)
+    np.testing.assert_allclose(g[0][1], c.ctrl[-1, :3], atol=1e-6)
+
+
 def test_forward_edge_cases():
     rng = np.random.default_rng(4)
     # Bezier nets (n = p), samples exactly on uniform knots, a double interior knot,
