@@ -213,21 +213,48 @@ __device__ __forceinline__ void curve_body(const KParams& kp, int t, unsigned ch
     const int o0 = 4 * (0 ^ swz), o1 = 4 * (1 ^ swz), o2 = 4 * (2 ^ swz), o3 = 4 * (3 ^ swz);
     auto word = [&](int w) { return ((w < 4) ? o1 : (w < 8) ? o2 : o3) + (w & 3); };
     // one sample: span, basis, point, MSE and the adjoint accumulations
-    auto process = [&](int b, float u, float gx, float gy, float gz, float* rb, int j) {
-        if (!(u >= ulo && u <= uhi)) err |= kErrDomain;
-        if (u < uprev) err |= kErrOrder;
-        uprev = u;
+    // Samples past the lane's end (the last active lane's short tail, lanes without
+    // samples) run the body too, as no-ops: every lane takes the same path, so the
+    // window step below is a warp-uniform branch.
+    auto process = [&](int b, float u, float gx, float gy, float gz, float* rb, int j, bool valid) {
+        if (valid) {
+            if (!(u >= ulo && u <= uhi)) err |= kErrDomain;
+            if (u < uprev) err |= kErrOrder;
+            uprev = u;
+        }
         u = fminf(fmaxf(u, ulo), uhi);
-        // The samples are non-decreasing, so the span only moves forward, mostly by
-        // one knot: step it a few knots (the same largest k with U_k <= u) before
-        // falling back to the binary search.  Lanes change span at different
-        // samples, so whatever this costs, the warp pays at almost every sample.
-        int s = cur;
+        // The samples are non-decreasing, so the span only moves forward, almost always
+        // by one knot.  Lanes change span at different samples; a loop per lane made
+        // the warp run it at almost every sample, so the one-knot step is taken by all
+        // lanes together (selects), and only a sample more than one span ahead falls
+        // back to the binary search and the per-lane loop.
+        const bool adv = valid && cur < n && !(u < s_kn[cur + 1]);
+        if (__any_sync(0xffffffffu, adv)) {
+            if (adv) {
+                retire_row(cur - P, tau[0]);
+                if constexpr (KNOTS) retire_knot(cur - P + 1, kacc[0]);
+            }
 #pragma unroll
-        for (int k = 0; k < 2; ++k)
-            if (s < n && !(u < s_kn[s + 1])) ++s;
-        if (s < n && !(u < s_kn[s + 1])) s = find_span(n, P, u, s_kn);
-        advance(s);
+            for (int r = 0; r < P; ++r) {
+                Qw[r] = adv ? Qw[r + 1] : Qw[r];
+                tau[r] = adv ? tau[r + 1] : tau[r];
+            }
+            tau[P] = adv ? f4zero() : tau[P];
+            if constexpr (KNOTS) {
+#pragma unroll
+                for (int k = 0; k + 1 < KW; ++k) kacc[k] = adv ? kacc[k + 1] : kacc[k];
+                kacc[KW - 1] = adv ? 0.f : kacc[KW - 1];
+            }
+            if (adv) {
+                ++cur;
+                Qw[P] = s_net[cur];
+            }
+            const bool more = adv && cur < n && !(u < s_kn[cur + 1]);
+            if (__any_sync(0xffffffffu, more)) {
+                if (more) advance(find_span(n, P, u, s_kn));
+            }
+        }
+        const int s = cur < 0 ? P : cur;   // lanes without samples compute on a valid span
         float N[PB];
         basis_funs<P>(s, u, s_kn, N);
         float4 Cw = f4zero();
@@ -235,7 +262,7 @@ __device__ __forceinline__ void curve_body(const KParams& kp, int t, unsigned ch
         for (int r = 0; r < PB; ++r) Cw = fma4(N[r], Qw[r], Cw);
         const float inv = rcp_approx(Cw.w);
         const float Sx = Cw.x * inv, Sy = Cw.y * inv, Sz = Cw.z * inv;
-        if (has_pts) {
+        if (has_pts && valid) {
             if constexpr (kStage) {
                 rb[word(3 * j)] = Sx; rb[word(3 * j + 1)] = Sy; rb[word(3 * j + 2)] = Sz;
             } else {
@@ -245,12 +272,12 @@ __device__ __forceinline__ void curve_body(const KParams& kp, int t, unsigned ch
         }
         float ginv = inv;
         if constexpr (MSE) {
-            gx = Sx - gx; gy = Sy - gy; gz = Sz - gz;
+            gx = valid ? Sx - gx : 0.f; gy = valid ? Sy - gy : 0.f; gz = valid ? Sz - gz : 0.f;
             lossacc = fmaf(gx, gx, fmaf(gy, gy, fmaf(gz, gz, lossacc)));
             ginv *= gsc;
         }
         const float lx = gx * ginv, ly = gy * ginv, lz = gz * ginv;
-        const float4 lam = make_float4(lx, ly, lz, -fmaf(Sx, lx, fmaf(Sy, ly, Sz * lz)));
+        const float4 lam = valid ? make_float4(lx, ly, lz, -fmaf(Sx, lx, fmaf(Sy, ly, Sz * lz))) : f4zero();
 #pragma unroll
         for (int r = 0; r < PB; ++r) tau[r] = fma4(N[r], lam, tau[r]);
         if constexpr (KNOTS) {
@@ -274,12 +301,10 @@ __device__ __forceinline__ void curve_body(const KParams& kp, int t, unsigned ch
         // instruction fetch than it saves)
 #pragma unroll 1
         for (int j = 0; j < R; ++j) {
-            if (bb + j < b1) {
-                float g[3];
+            float g[3];
 #pragma unroll
-                for (int c = 0; c < 3; ++c) g[c] = rb[word(3 * j + c)];
-                process(bb + j, rb[o0 + j], g[0], g[1], g[2], rb, j);
-            }
+            for (int c = 0; c < 3; ++c) g[c] = rb[word(3 * j + c)];
+            process(bb + j, rb[o0 + j], g[0], g[1], g[2], rb, j, bb + j < b1);
         }
         if (kStage && has_pts) {   // sample j's targets were read before its point was written
             float* o = kp.pts + 3 * (it.pts + (long long)bb);
