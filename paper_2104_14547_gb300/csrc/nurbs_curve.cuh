@@ -68,9 +68,88 @@ __device__ __forceinline__ void st_global16(float* dst, const float* src)
     *reinterpret_cast<float4*>(dst) = *reinterpret_cast<const float4*>(src);
 }
 
-// Gradient kernels (backward, MSE, fit step): the per-lane window walk above.
+// This lane's share of a curve's samples: [b0, b1), a whole number of rounds of
+// kCurveRound samples (the last active lane may be short).
+struct CurveLane {
+    int nb, b0, b1, rounds;
+    bool al16;   // parameters and targets start on 16-byte boundaries
+};
+
+__device__ __forceinline__ CurveLane curve_lane(const ItemDev& it, int lane)
+{
+    CurveLane c;
+    const int ns = it.nv;
+    c.nb = (ns + 32 * kCurveRound - 1) / (32 * kCurveRound) * kCurveRound;
+    c.b0 = min(lane * c.nb, ns);
+    c.b1 = min(c.b0 + c.nb, ns);
+    c.rounds = c.nb / kCurveRound;
+    c.al16 = ((it.param_v & 3) == 0) && ((it.pts & 3) == 0);
+    return c;
+}
+
+// Stage round k of this lane's parameters and targets: one cp.async group (empty
+// past the lane's last round).
+__device__ __forceinline__ void curve_issue(const KParams& kp, const ItemDev& it, const CurveLane& c, float* s_ring,
+                                            int lane, int k)
+{
+    constexpr int R = kCurveRound;
+    if (k < c.rounds) {
+        const float* __restrict__ gu = kp.params + it.param_v;
+        const float* __restrict__ gt = kp.gin + 3 * it.pts;
+        const int swz = (lane >> 1) & 3;
+        const int bb = c.b0 + k * R;
+        float* dst = s_ring + ((k & (kCurveStages - 1)) * 32 + lane) * 16;
+        if (c.al16 && bb + R <= c.b1) {
+            cp_async16(dst + 4 * (0 ^ swz), gu + bb);
+            cp_async16(dst + 4 * (1 ^ swz), gt + 3 * bb);
+            cp_async16(dst + 4 * (2 ^ swz), gt + 3 * bb + 4);
+            cp_async16(dst + 4 * (3 ^ swz), gt + 3 * bb + 8);
+        } else {
+#pragma unroll
+            for (int j = 0; j < R; ++j) {
+                if (bb + j < c.b1) {
+                    cp_async4(dst + 4 * (0 ^ swz) + j, gu + bb + j);
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        const int w = 3 * j + q;   // target word of the round
+                        cp_async4(dst + 4 * ((1 + w / 4) ^ swz) + (w & 3), gt + 3 * (bb + j) + q);
+                    }
+                }
+            }
+        }
+    }
+    cp_async_commit();
+}
+
+// Issue the staging of curve t: its knots and control net (one group), then its
+// first kCurveStages rounds.  A warp stages its next curve while its final pass of
+// the current one runs: that pass reads none of these buffers.
+template <int P>
+__device__ __forceinline__ void curve_stage(const KParams& kp, int t, unsigned char* wsm)
+{
+    const int lane = threadIdx.x & 31;
+    const int mc = kp.c_mc;
+    float* s_kn = reinterpret_cast<float*>(wsm);
+    float4* s_net = reinterpret_cast<float4*>(wsm + curve_off_net(mc, P));
+    float* s_ring = reinterpret_cast<float*>(wsm + curve_off_ring(mc, P));
+    const ItemDev it = kp.items[kp.tiles[t].item];
+    const int nc = it.m1, nk = nc + P + 1;
+    const float* __restrict__ gU = kp.knots + it.knot_v;
+    const float4* __restrict__ gP = kp.ctrl + it.ctrl;
+    for (int k = lane; k < nk; k += 32) cp_async4(s_kn + k, gU + k);
+    for (int i = lane; i < nc; i += 32)
+        cp_async16(reinterpret_cast<float*>(s_net + i), reinterpret_cast<const float*>(gP + i));
+    cp_async_commit();
+    const CurveLane c = curve_lane(it, lane);
+#pragma unroll
+    for (int k = 0; k < kCurveStages; ++k) curve_issue(kp, it, c, s_ring, lane, k);
+}
+
+// Gradient kernels (backward, MSE, fit step): the per-lane window walk above.  The
+// curve's staging (curve_stage) was issued before the call; returns the warp's next
+// curve, already staged.
 template <int P, bool KNOTS, bool MSE>
-__device__ __forceinline__ void curve_body(const KParams& kp, int t, unsigned char* wsm)
+__device__ __forceinline__ int curve_body(const KParams& kp, int t, unsigned char* wsm)
 {
     constexpr int PB = P + 1;
     constexpr int KW = 2 * P;
@@ -90,51 +169,14 @@ __device__ __forceinline__ void curve_body(const KParams& kp, int t, unsigned ch
     const int item = kp.tiles[t].item;
     const ItemDev it = kp.items[item];
     const int nc = it.m1, n = nc - 1, ns = it.nv, nk = nc + P + 1;
-    const float* __restrict__ gU = kp.knots + it.knot_v;
     const float* __restrict__ gu = kp.params + it.param_v;
-    const float4* __restrict__ gP = kp.ctrl + it.ctrl;
-    const float* __restrict__ gt = kp.gin + 3 * it.pts;
 
-    for (int k = lane; k < nk; k += 32) cp_async4(s_kn + k, gU + k);
-    for (int i = lane; i < nc; i += 32)
-        cp_async16(reinterpret_cast<float*>(s_net + i), reinterpret_cast<const float*>(gP + i));
-    cp_async_commit();
-
-    // this lane's samples [b0, b1): a whole number of rounds each (the last lane may be short)
-    const int nb = (ns + 32 * R - 1) / (32 * R) * R;
-    const int b0 = min(lane * nb, ns), b1 = min(b0 + nb, ns);
+    const CurveLane cl = curve_lane(it, lane);
+    const int nb = cl.nb, b0 = cl.b0, b1 = cl.b1, rounds = cl.rounds;
     const bool act = b0 < b1;
-    const int rounds = nb / R;
     const int nact = nb > 0 ? (ns + nb - 1) / nb : 0;   // active lanes form a prefix
-    const bool al16 = ((it.param_v & 3) == 0) && ((it.pts & 3) == 0);
     const int swz = (lane >> 1) & 3;
-    auto issue = [&](int k) {
-        if (k < rounds) {
-            const int bb = b0 + k * R;
-            float* dst = s_ring + ((k & (kCurveStages - 1)) * 32 + lane) * 16;
-            if (al16 && bb + R <= b1) {
-                cp_async16(dst + 4 * (0 ^ swz), gu + bb);
-                cp_async16(dst + 4 * (1 ^ swz), gt + 3 * bb);
-                cp_async16(dst + 4 * (2 ^ swz), gt + 3 * bb + 4);
-                cp_async16(dst + 4 * (3 ^ swz), gt + 3 * bb + 8);
-            } else {
-#pragma unroll
-                for (int j = 0; j < R; ++j) {
-                    if (bb + j < b1) {
-                        cp_async4(dst + 4 * (0 ^ swz) + j, gu + bb + j);
-#pragma unroll
-                        for (int c = 0; c < 3; ++c) {
-                            const int w = 3 * j + c;   // target word of the round
-                            cp_async4(dst + 4 * ((1 + w / 4) ^ swz) + (w & 3), gt + 3 * (bb + j) + c);
-                        }
-                    }
-                }
-            }
-        }
-        cp_async_commit();
-    };
-#pragma unroll
-    for (int k = 0; k < kCurveStages; ++k) issue(k);
+    auto issue = [&](int k) { curve_issue(kp, it, cl, s_ring, lane, k); };
     cp_async_wait<kCurveStages>();   // the knots and the control net
     __syncwarp();
     for (int i = lane; i < nc; i += 32) s_net[i] = homog(s_net[i]);   // kept as Pw from here on
@@ -334,7 +376,13 @@ __device__ __forceinline__ void curve_body(const KParams& kp, int t, unsigned ch
 #pragma unroll
     for (int o = 16; o >= 1; o >>= 1) lossacc += __shfl_xor_sync(0xffffffffu, lossacc, o);
     if (lane == 0 && kp.loss_items != nullptr) kp.loss_items[item] = lossacc;
-    __syncwarp();
+    // The warp's next curve is taken now, when this one has only its final pass left
+    // (so the queue still hands curves to the warps that finish first), and staged
+    // while that pass runs.
+    int nq = 0;
+    if (lane == 0) nq = kp.t0 + (int)gridDim.x * kCurveWarps + (int)atomicAdd(kp.queue, 1u);
+    const int nt = __shfl_sync(0xffffffffu, nq, 0);   // every lane is past its reads of knots, net and ring
+    if (nt < kp.t1) curve_stage<P>(kp, nt, wsm);
 
     // First lane whose last span reaches index x (spans of active lanes are sorted).
     auto first_lane = [&](int x) {
@@ -401,6 +449,7 @@ __device__ __forceinline__ void curve_body(const KParams& kp, int t, unsigned ch
         }
     }
     __syncwarp();
+    return nt;
 }
 
 // Forward (points, and tangents when DER): no adjoint to accumulate, so no
@@ -515,12 +564,16 @@ __global__ void __launch_bounds__(32 * kCurveWarps, curve_min_blocks<P, GRAD>())
     unsigned char* wsm = reinterpret_cast<unsigned char*>(smem4) + warp * kp.c_wbytes;
     // the first curve of each warp is its own index; later ones come from the queue
     int t = kp.t0 + (int)blockIdx.x * kCurveWarps + warp;
-    while (t < kp.t1) {
-        if constexpr (GRAD) curve_body<P, KNOTS, MSE>(kp, t, wsm);
-        else curve_eval_body<P, DER>(kp, t, wsm);
-        int nt = 0;
-        if (lane == 0) nt = kp.t0 + (int)gridDim.x * kCurveWarps + (int)atomicAdd(kp.queue, 1u);
-        t = __shfl_sync(0xffffffffu, nt, 0);
+    if constexpr (GRAD) {
+        if (t < kp.t1) curve_stage<P>(kp, t, wsm);
+        while (t < kp.t1) t = curve_body<P, KNOTS, MSE>(kp, t, wsm);
+    } else {
+        while (t < kp.t1) {
+            curve_eval_body<P, DER>(kp, t, wsm);
+            int nt = 0;
+            if (lane == 0) nt = kp.t0 + (int)gridDim.x * kCurveWarps + (int)atomicAdd(kp.queue, 1u);
+            t = __shfl_sync(0xffffffffu, nt, 0);
+        }
     }
     __syncthreads();
     // the last CTA out rearms the queue for the next launch on this workspace
