@@ -9,6 +9,8 @@
 #include <new>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/nurbs.h"
 #include "nurbs_curve.cuh"
 #include "nurbs_kernel.cuh"
@@ -18,6 +20,16 @@ using namespace nurbs;
 namespace {
 
 thread_local int32_t g_last_cuda_error = 0;
+
+// An NVTX range named after the entry point, around its host work and launches
+// (profilers can filter on it, e.g. ncu --nvtx); with no tool attached a push and
+// a pop cost a pointer test each.
+struct NvtxScope {
+    explicit NvtxScope(const char* name) { nvtxRangePushA(name); }
+    ~NvtxScope() { nvtxRangePop(); }
+    NvtxScope(const NvtxScope&) = delete;
+    NvtxScope& operator=(const NvtxScope&) = delete;
+};
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 inline int align4(int x) { return (x + 3) & ~3; }
@@ -572,12 +584,14 @@ static nurbs_status eval_common(const nurbs_plan* pl, int32_t kind, const float*
 nurbs_status nurbs_eval_surface(const nurbs_plan* plan, const float* knots, const float* ctrl,
                                 const float* params, float* pts, nurbs_stream_t stream)
 {
+    NvtxScope nvtx_("nurbs_eval_surface");
     return eval_common(plan, NURBS_KIND_SURFACE, knots, ctrl, params, pts, stream);
 }
 
 nurbs_status nurbs_eval_curve(const nurbs_plan* plan, const float* knots, const float* ctrl,
                               const float* params, float* pts, nurbs_stream_t stream)
 {
+    NvtxScope nvtx_("nurbs_eval_curve");
     return eval_common(plan, NURBS_KIND_CURVE, knots, ctrl, params, pts, stream);
 }
 
@@ -607,12 +621,14 @@ nurbs_status nurbs_eval_surface_derivs(const nurbs_plan* plan, const float* knot
                                        const float* params, float* pts, float* du, float* dv, float* normals,
                                        nurbs_stream_t stream)
 {
+    NvtxScope nvtx_("nurbs_eval_surface_derivs");
     return derivs_common(plan, NURBS_KIND_SURFACE, knots, ctrl, params, pts, du, dv, normals, stream);
 }
 
 nurbs_status nurbs_eval_curve_derivs(const nurbs_plan* plan, const float* knots, const float* ctrl,
                                      const float* params, float* pts, float* tangents, nurbs_stream_t stream)
 {
+    NvtxScope nvtx_("nurbs_eval_curve_derivs");
     // a curve runs as the v direction of its item: its tangent is the v-derivative
     return derivs_common(plan, NURBS_KIND_CURVE, knots, ctrl, params, pts, nullptr, tangents, nullptr, stream);
 }
@@ -664,6 +680,7 @@ nurbs_status nurbs_backward(const nurbs_plan* plan, const float* knots, const fl
                             const float* params, const float* grad_pts, float* grad_ctrl,
                             float* grad_knots, nurbs_stream_t stream)
 {
+    NvtxScope nvtx_("nurbs_backward");
     return grad_common(plan, knots, ctrl, nullptr, params, grad_pts, 0, nullptr, grad_ctrl, grad_knots,
                        nullptr, 0.f, nullptr, nullptr, nullptr, 0, stream);
 }
@@ -673,6 +690,7 @@ nurbs_status nurbs_mse_fwd_bwd(const nurbs_plan* plan, const float* knots, const
                                float* grad_ctrl, float* grad_knots, float* loss_items,
                                float grad_scale, nurbs_stream_t stream)
 {
+    NvtxScope nvtx_("nurbs_mse_fwd_bwd");
     return grad_common(plan, knots, ctrl, nullptr, params, target, 1, pts, grad_ctrl, grad_knots,
                        loss_items, grad_scale, nullptr, nullptr, nullptr, 0, stream);
 }
@@ -683,6 +701,7 @@ nurbs_status nurbs_fit_step(const nurbs_plan* plan, const float* knots, float* c
                             float grad_scale, float* loss_items, float* grad_knots,
                             nurbs_stream_t stream)
 {
+    NvtxScope nvtx_("nurbs_fit_step");
     if (hp == nullptr) return NURBS_ERR_ARG;
     return grad_common(plan, knots, ctrl, ctrl, params, target, 1, pts, nullptr, grad_knots,
                        loss_items, grad_scale, adam_m, adam_v, hp, step, stream);
@@ -753,6 +772,7 @@ extern "C" nurbs_status nurbs_mse_fwd_bwd_noalloc(const nurbs_plan* cpl, const f
                                                   float* grad_ctrl, float* grad_knots, float* loss_items,
                                                   float grad_scale, nurbs_stream_t stream)
 {
+    NvtxScope nvtx_("nurbs_mse_fwd_bwd_noalloc");
     if (cpl == nullptr) return NURBS_ERR_ARG;
     if (cpl->ws_bytes > (size_t)NURBS_NOALLOC_SCRATCH_BYTES) return NURBS_ERR_WORKSPACE;
     if (cpl->tiles.empty()) return NURBS_OK;

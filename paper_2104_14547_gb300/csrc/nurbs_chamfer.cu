@@ -20,6 +20,7 @@
 //                  placement, then each bucket is sorted by j, so the sums keep a
 //                  fixed order.  Without scratch, each P_i scans the pair's whole
 //                  nearest-point map instead.
+#include <nvtx3/nvToolsExt.h>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -302,6 +303,8 @@ extern "C" nurbs_status nurbs_chamfer(int32_t count, const int64_t* p_off, const
                                       float* grad_hd, int32_t* scratch, int64_t total_p, int64_t total_q,
                                       nurbs_stream_t stream)
 {
+    nvtxRangePushA("nurbs_chamfer");
+    struct Pop { ~Pop() { nvtxRangePop(); } } pop_;
     if (count < 0 || max_p < 0 || max_q < 0) return NURBS_ERR_ARG;
     if (count == 0) return NURBS_OK;
     if (count > 65535) return NURBS_ERR_SIZE;
