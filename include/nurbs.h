@@ -294,7 +294,8 @@ nurbs_status nurbs_fit_step(const nurbs_plan* plan, const float* knots, float* c
  *     clears its counters first, and calls that overlap on the GPU (other streams,
  *     other host threads) race on it and give wrong results.
  *   - The first call on a device looks up the array's device address (once per
- *     device, with that device current).
+ *     device, with that device current).  Make that first call on each device
+ *     before any stream capture begins.
  *   - Device-side data errors (knots, domain, sample order) go to an error word
  *     at the head of the array, which calls do not clear: it collects the checks
  *     of every call until nurbs_noalloc_get_error reads it.  nurbs_plan_get_error

@@ -9,7 +9,9 @@ from __future__ import annotations
 import ctypes
 import os
 import subprocess
+import tempfile
 import threading
+import time
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
 _ROOT = os.path.dirname(_PKG)
@@ -31,8 +33,22 @@ def _nvcc() -> str:
     return cand if os.path.exists(cand) else "nvcc"
 
 
-def _sources():
-    return sorted(os.path.join(_CSRC, f) for f in os.listdir(_CSRC) if f.endswith(".cu"))
+def _jobs():
+    """(source, object, extra flags) per translation unit: k_tiles.cu once per
+    (u degree, variant) pair, every other .cu once."""
+    jobs = []
+    for f in sorted(os.listdir(_CSRC)):
+        if not f.endswith(".cu"):
+            continue
+        src = os.path.join(_CSRC, f)
+        if f == "k_tiles.cu":
+            for p in range(6):
+                for v in range(6):
+                    jobs.append((src, os.path.join(_BUILD, f"k_tiles_p{p}_v{v}.o"),
+                                 [f"-DNURBS_P={p}", f"-DNURBS_V={v}"]))
+        else:
+            jobs.append((src, os.path.join(_BUILD, f[:-3] + ".o"), []))
+    return jobs
 
 
 def _deps():
@@ -46,19 +62,32 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if not force and os.path.exists(SO_PATH) and os.path.getmtime(SO_PATH) >= newest:
         return SO_PATH
     nvcc = _nvcc()
-    procs, objs = [], []
-    for src in _sources():
-        obj = os.path.join(_BUILD, os.path.basename(src)[:-3] + ".o")
-        objs.append(obj)
-        cmd = [nvcc, *ARCH, *NVCC_FLAGS, "-c", src, "-o", obj]
-        procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
-    errors = []
-    for cmd, p in procs:
-        out, _ = p.communicate()
-        if verbose and out:
-            print(out.decode(errors="replace"))
-        if p.returncode != 0:
-            errors.append(" ".join(cmd) + "\n" + out.decode(errors="replace"))
+    # at most one nvcc per core, the tile kernels (the longest jobs) first
+    jobs = sorted(_jobs(), key=lambda j: "k_tiles" not in j[0])
+    objs = [o for _, o, _ in jobs]
+    pending = list(jobs)
+    running, errors = [], []
+    ncpu = max(1, os.cpu_count() or 1)
+    while pending or running:
+        while pending and len(running) < ncpu:
+            src, obj, extra = pending.pop(0)
+            cmd = [nvcc, *ARCH, *NVCC_FLAGS, *extra, "-c", src, "-o", obj]
+            log = tempfile.TemporaryFile()
+            running.append((cmd, log, subprocess.Popen(cmd, stdout=log, stderr=subprocess.STDOUT)))
+        done = [r for r in running if r[2].poll() is not None]
+        if not done:
+            time.sleep(0.05)
+            continue
+        for r in done:
+            running.remove(r)
+            cmd, log, p = r
+            log.seek(0)
+            out = log.read()
+            log.close()
+            if verbose and out:
+                print(out.decode(errors="replace"))
+            if p.returncode != 0:
+                errors.append(" ".join(cmd) + "\n" + out.decode(errors="replace"))
     if errors:
         raise RuntimeError("libnurbs build failed:\n" + "\n".join(errors))
     cudalib = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "lib64")

@@ -420,14 +420,24 @@ namespace {
 
 KernelVariant variant_for(int v, int p, int q)
 {
-    switch (p) {
-        case 0: return variant_p0(v, q);
-        case 1: return variant_p1(v, q);
-        case 2: return variant_p2(v, q);
-        case 3: return variant_p3(v, q);
-        case 4: return variant_p4(v, q);
-        default: return variant_p5(v, q);
+#define NURBS_TILE_V(pp)                                   \
+    switch (v) {                                           \
+        case 0: return tile_variant_p##pp##_v0(q);         \
+        case 1: return tile_variant_p##pp##_v1(q);         \
+        case 2: return tile_variant_p##pp##_v2(q);         \
+        case 3: return tile_variant_p##pp##_v3(q);         \
+        case 4: return tile_variant_p##pp##_v4(q);         \
+        default: return tile_variant_p##pp##_v5(q);        \
     }
+    switch (p) {
+        case 0: NURBS_TILE_V(0)
+        case 1: NURBS_TILE_V(1)
+        case 2: NURBS_TILE_V(2)
+        case 3: NURBS_TILE_V(3)
+        case 4: NURBS_TILE_V(4)
+        default: NURBS_TILE_V(5)
+    }
+#undef NURBS_TILE_V
 }
 
 // Kernel, block, shared memory and queue slot of one group for variant v.

@@ -66,13 +66,19 @@ struct VariantOf {
 
 // variant: 0 forward; 1 / 2 backward from dL/dS without / with knot gradients;
 // 3 / 4 the same from an MSE target; 5 forward with tangents and normals.
-// Defined per u degree in k_p<P>.cu.
-KernelVariant variant_p0(int v, int q);
-KernelVariant variant_p1(int v, int q);
-KernelVariant variant_p2(int v, int q);
-KernelVariant variant_p3(int v, int q);
-KernelVariant variant_p4(int v, int q);
-KernelVariant variant_p5(int v, int q);
+// tile_variant_p<P>_v<V>(q) is defined in k_tiles.cu compiled with NURBS_P = P,
+// NURBS_V = V; tile_variant(p, v, q) (nurbs_api.cu) dispatches over them.
+#define NURBS_DECLARE_TILE_P(p)                                                         \
+    KernelVariant tile_variant_p##p##_v0(int q); KernelVariant tile_variant_p##p##_v1(int q); \
+    KernelVariant tile_variant_p##p##_v2(int q); KernelVariant tile_variant_p##p##_v3(int q); \
+    KernelVariant tile_variant_p##p##_v4(int q); KernelVariant tile_variant_p##p##_v5(int q);
+NURBS_DECLARE_TILE_P(0)
+NURBS_DECLARE_TILE_P(1)
+NURBS_DECLARE_TILE_P(2)
+NURBS_DECLARE_TILE_P(3)
+NURBS_DECLARE_TILE_P(4)
+NURBS_DECLARE_TILE_P(5)
+#undef NURBS_DECLARE_TILE_P
 // Curve kernels (one warp per curve) of degree p, defined in k_curve.cu.
 KernelVariant curve_variant(int v, int p);
 
