@@ -87,14 +87,24 @@ struct KParams {
 
 __device__ __forceinline__ float4 f4zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
 
+// float4 arithmetic on packed FP32 pairs (FFMA2 / FMUL2, sm_100 and later): one
+// instruction per two components, each component rounded as the scalar operation.
+__device__ __forceinline__ float2 lo2(float4 a) { return make_float2(a.x, a.y); }
+__device__ __forceinline__ float2 hi2(float4 a) { return make_float2(a.z, a.w); }
+
 __device__ __forceinline__ float4 fma4(float s, float4 a, float4 c)
 {
-    return make_float4(fmaf(s, a.x, c.x), fmaf(s, a.y, c.y), fmaf(s, a.z, c.z), fmaf(s, a.w, c.w));
+    const float2 s2 = make_float2(s, s);
+    const float2 l = __ffma2_rn(s2, lo2(a), lo2(c));
+    const float2 h = __ffma2_rn(s2, hi2(a), hi2(c));
+    return make_float4(l.x, l.y, h.x, h.y);
 }
 
+// a.b as (a.x b.x + a.z b.z) + (a.y b.y + a.w b.w)
 __device__ __forceinline__ float dot4(float4 a, float4 b)
 {
-    return fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, a.w * b.w)));
+    const float2 p = __ffma2_rn(lo2(a), lo2(b), __fmul2_rn(hi2(a), hi2(b)));
+    return p.x + p.y;
 }
 
 // Homogeneous control point (w x, w y, w z, w) of Sec. 3.1 step 3.
