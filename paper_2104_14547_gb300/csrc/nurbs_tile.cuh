@@ -265,26 +265,33 @@ __device__ __forceinline__ void finish_ctrl(const KParams& kp, const ItemDev& it
 // [jlo, jlo+cw) were written.  The overflow rows are added into the net block in
 // unit order, then every control point is finished (its Cartesian point read from
 // global memory), four per thread per pass with their loads issued first.
-__device__ __forceinline__ void final_ctrl_smem(const KParams& kp, const ItemDev& it, int nwr, int pb,
-                                                const int* s_units, int jlo, int cw)
+// Adds unit u's overflow block into the net block.
+__device__ __forceinline__ void merge_overflow_smem(const KParams& kp, const ItemDev& it, int u, int pb,
+                                                    const int* s_units, int jlo, int cw)
+{
+    extern __shared__ float4 smem4[];
+    unsigned char* smem = reinterpret_cast<unsigned char*>(smem4);
+    const int m1 = it.m1, ncp = it.n1 * m1, bs = blockDim.x;
+    float4* sB = reinterpret_cast<float4*>(smem + kp.off_sa);
+    const float4* sO = sB + ncp;
+    const int ilo = s_units[3 * u], nr = s_units[3 * u + 1], pm = s_units[3 * u + 2];
+    const int nov = nr > 0 ? max(0, min(ilo + nr - 1, pm) - ilo + 1) : 0;
+    for (int x = threadIdx.x; x < nov * cw; x += bs) {
+        const int ii = x / cw, jj = x - ii * cw;
+        float4& d = sB[(ilo + ii) * m1 + jlo + jj];
+        const float4 v = sO[(u * pb + ii) * m1 + jlo + jj];
+        d.x += v.x; d.y += v.y; d.z += v.z; d.w += v.w;
+    }
+}
+
+// Finishes every control point of the item from the (merged) net block.
+__device__ __forceinline__ void finish_ctrl_smem(const KParams& kp, const ItemDev& it)
 {
     extern __shared__ float4 smem4[];
     unsigned char* smem = reinterpret_cast<unsigned char*>(smem4);
     if (kp.grad_ctrl == nullptr && !kp.fit) return;
-    const int m1 = it.m1, ncp = it.n1 * m1, bs = blockDim.x;
-    float4* sB = reinterpret_cast<float4*>(smem + kp.off_sa);
-    const float4* sO = sB + ncp;
-    for (int u = 1; u < nwr; ++u) {
-        const int ilo = s_units[3 * u], nr = s_units[3 * u + 1], pm = s_units[3 * u + 2];
-        const int nov = nr > 0 ? max(0, min(ilo + nr - 1, pm) - ilo + 1) : 0;
-        for (int x = threadIdx.x; x < nov * cw; x += bs) {
-            const int ii = x / cw, jj = x - ii * cw;
-            float4& d = sB[(ilo + ii) * m1 + jlo + jj];
-            const float4 v = sO[(u * pb + ii) * m1 + jlo + jj];
-            d.x += v.x; d.y += v.y; d.z += v.z; d.w += v.w;
-        }
-        __syncthreads();
-    }
+    const int ncp = it.n1 * it.m1, bs = blockDim.x;
+    const float4* sB = reinterpret_cast<const float4*>(smem + kp.off_sa);
     float lr_t, isb2;
     adam_corrections(kp, it, lr_t, isb2);
     constexpr int EB = 4;
@@ -306,6 +313,17 @@ __device__ __forceinline__ void final_ctrl_smem(const KParams& kp, const ItemDev
             if (e < ncp) finish_point(kp, it.ctrl + e, c[k], a[k], mm[k], vv[k], lr_t, isb2);
         }
     }
+}
+
+__device__ __forceinline__ void final_ctrl_smem(const KParams& kp, const ItemDev& it, int nwr, int pb,
+                                                const int* s_units, int jlo, int cw)
+{
+    if (kp.grad_ctrl == nullptr && !kp.fit) return;
+    for (int u = 1; u < nwr; ++u) {
+        merge_overflow_smem(kp, it, u, pb, s_units, jlo, cw);
+        __syncthreads();
+    }
+    finish_ctrl_smem(kp, it);
 }
 
 // ---------------------------------------------------------------------------
@@ -496,12 +514,10 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
         cp_async_commit();
         isrc += 3 * it.nv;
     };
-    if constexpr (GRAD) {
-        for (int d = 0; d < nring; ++d) issue_row(ra + d);
-    }
-    __syncthreads();
 
-    // ---- stage the knot vectors and this tile's samples in shared memory (one round trip)
+    // ---- staging, in three kinds of cp.async groups: the knot vectors and this tile's
+    // samples (the tables below need only these), then the control net, then the first
+    // rows of the ring.  The tables are built while the net and the ring rows land.
     float* s_knU = reinterpret_cast<float*>(smem + kp.off_knots);
     float* s_knV = s_knU + ((P > 0) ? ((it.n1 + P + 1 + 3) & ~3) : 0);
     const int nU = (P > 0) ? it.n1 + P + 1 : 0, nV = it.m1 + Q + 1;
@@ -512,6 +528,7 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
             for (int r = tid; r < nrows; r += bs) cp_async4(s_u + r, kp.params + it.param_u + tl.row0 + r);
         for (int c = tid; c < ncols; c += bs) cp_async4(s_v + c, kp.params + it.param_v + tl.col0 + c);
     }
+    cp_async_commit();
     // the whole control net rides along when it fits (else the tile's window follows
     // later); once landed it is kept as homogeneous points Pw = (w x, w y, w z, w)
     float4* s_win = reinterpret_cast<float4*>(smem + kp.off_win);
@@ -523,7 +540,12 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
             cp_async16(reinterpret_cast<float*>(s_win + e), reinterpret_cast<const float*>(src + e));
     }
     cp_async_commit();
-    cp_async_wait<0>();
+    if constexpr (GRAD) {
+        for (int d = 0; d < nring; ++d) issue_row(ra + d);
+        if (nring == kRing) cp_async_wait<kRing + 1>(); else cp_async_wait<kRing / 2 + 1>();
+    } else {
+        cp_async_wait<1>();
+    }
     __syncthreads();
 
     // ---- one pass over rows and columns: device checks (knot vectors once per item,
@@ -533,8 +555,6 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
     const float ulo = (P > 0) ? s_knU[P] : 0.f, uhi = (P > 0) ? s_knU[n + 1] : 0.f;
     const float vlo = s_knV[Q], vhi = s_knV[m + 1];
     const int npro_r = empty ? 0 : nrows, npro_c = empty ? 0 : ncols;   // empty tiles skip the tables
-    if (net_staged)
-        for (int e = tid; e < ncp; e += bs) s_win[e] = homog(s_win[e]);
     if (GRAD && it.smemA) {   // the shared adjoint block of a single-tile item starts at zero
         float4* sB = reinterpret_cast<float4*>(smem + kp.off_sa);
         for (int e = tid; e < ncp; e += bs) sB[e] = f4zero();
@@ -690,10 +710,19 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
             }
         }
     }
-    if (win_only) cp_async_wait<0>();
-    __syncthreads();
     if (win_only) {
-        for (int e = tid; e < rw_t * cw_t; e += bs) s_win[e] = homog(s_win[e]);
+        cp_async_wait<0>();
+    } else if (net_staged) {   // the net's group; only the ring rows may still be in flight
+        if constexpr (GRAD) {
+            if (nring == kRing) cp_async_wait<kRing>(); else cp_async_wait<kRing / 2>();
+        } else {
+            cp_async_wait<0>();
+        }
+    }
+    __syncthreads();
+    if (win) {
+        const int nwin = net_staged ? ncp : rw_t * cw_t;
+        for (int e = tid; e < nwin; e += bs) s_win[e] = homog(s_win[e]);
         __syncthreads();
     }
 
@@ -1054,6 +1083,11 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
                 for (int K = tid; K < it.n1 + P + 1; K += bs) kp.grad_knots[it.knot_u + K] = 0.f;
             for (int K = tid; K < it.m1 + Q + 1; K += bs) kp.grad_knots[it.knot_v + K] = 0.f;
         }
+        // A single-tile item with its adjoint in shared memory and at most two units
+        // merges unit 1's overflow during the knot pass and finishes its control points
+        // during the knot sums (neither reads what the other writes).
+        const bool ctrl_early = KNOTS && !bad && single && it.smemA && nwr <= 2 &&
+                                (kp.grad_ctrl != nullptr || kp.fit);
         if constexpr (KNOTS) {
             if (!bad) {
                 const int nwc_valid = (ncols + 31) / 32;
@@ -1101,6 +1135,7 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
                         for (int k = 0; k < 2 * Q; ++k) s_dvc[c * KV + k] = dk[k];   // group 0's slot
                     }
                 }
+                if (ctrl_early && nwr == 2) merge_overflow_smem(kp, it, 1, PB, s_flag + 32, jlo_t, cw_t);
                 __syncthreads();
                 // Each knot's derivative: the rows (columns) whose span window holds knot k
                 // form a contiguous range; eight lanes sum it, lane-strided, then in a
@@ -1147,6 +1182,7 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
                     }
                 }
                 if (tid == 0) { sh[0] = ku_lo; sh[1] = nku; sh[2] = kv_lo; sh[3] = nkv; }
+                if (ctrl_early) finish_ctrl_smem(kp, it);
             } else if (tid == 0) {
                 sh[0] = 0; sh[1] = 0; sh[2] = 0; sh[3] = 0;
             }
@@ -1155,9 +1191,11 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
         }
         if (single) {
             // the only tile of its item: reduce its own units (shared memory or its slot)
-            __syncthreads();
-            if (it.smemA) final_ctrl_smem(kp, it, nwr, PB, s_flag + 32, jlo_t, cw_t);
-            else final_reduce(kp, tl.item, true);
+            if (!ctrl_early) {
+                __syncthreads();
+                if (it.smemA) final_ctrl_smem(kp, it, nwr, PB, s_flag + 32, jlo_t, cw_t);
+                else final_reduce(kp, tl.item, true);
+            }
         } else {
             // publish the partials (the barrier orders the CTA's writes before thread 0's
             // device-scope fence); the last tile of the item reduces them
