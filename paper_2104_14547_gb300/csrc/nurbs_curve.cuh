@@ -45,8 +45,9 @@ constexpr int kCurveCtrlCap = 256;    // control points per curve on this path (
 //   net    16 mc         the curve's control points (x, y, z, w)
 //   ring   2048 stages   [stages][32][4] float4: per lane one chunk of 4 parameters and three
 //                        chunks of 4 targets (x y z); lane L's chunk c sits at slot
-//                        c ^ ((L >> 1) & 3) so that the lanes' 128-bit reads of one
-//                        chunk hit 8 distinct bank groups per quarter warp
+//                        (c + ((L >> 1) & 3)) mod 4 so that the lanes' reads of one
+//                        chunk hit distinct bank groups per quarter warp, and word x
+//                        of the lane's 16 at (x + 4 ((L >> 1) & 3)) mod 16
 // The forward-only kernels (curve_eval_body) keep just the knots [0, 4 kc) and the
 // net as homogeneous points (16 mc).
 __host__ __device__ constexpr int curve_kc(int mc, int P) { return (mc + P + 1 + 3) & ~3; }
@@ -100,19 +101,19 @@ __device__ __forceinline__ void curve_issue(const KParams& kp, const ItemDev& it
         const int bb = c.b0 + k * R;
         float* dst = s_ring + ((k & (kCurveStages - 1)) * 32 + lane) * 16;
         if (c.al16 && bb + R <= c.b1) {
-            cp_async16(dst + 4 * (0 ^ swz), gu + bb);
-            cp_async16(dst + 4 * (1 ^ swz), gt + 3 * bb);
-            cp_async16(dst + 4 * (2 ^ swz), gt + 3 * bb + 4);
-            cp_async16(dst + 4 * (3 ^ swz), gt + 3 * bb + 8);
+            cp_async16(dst + 4 * (swz & 3), gu + bb);
+            cp_async16(dst + 4 * ((1 + swz) & 3), gt + 3 * bb);
+            cp_async16(dst + 4 * ((2 + swz) & 3), gt + 3 * bb + 4);
+            cp_async16(dst + 4 * ((3 + swz) & 3), gt + 3 * bb + 8);
         } else {
 #pragma unroll
             for (int j = 0; j < R; ++j) {
                 if (bb + j < c.b1) {
-                    cp_async4(dst + 4 * (0 ^ swz) + j, gu + bb + j);
+                    cp_async4(dst + ((j + 4 * swz) & 15), gu + bb + j);
 #pragma unroll
                     for (int q = 0; q < 3; ++q) {
                         const int w = 3 * j + q;   // target word of the round
-                        cp_async4(dst + 4 * ((1 + w / 4) ^ swz) + (w & 3), gt + 3 * (bb + j) + q);
+                        cp_async4(dst + ((4 + w + 4 * swz) & 15), gt + 3 * (bb + j) + q);
                     }
                 }
             }
@@ -252,8 +253,9 @@ __device__ __forceinline__ int curve_body(const KParams& kp, int t, unsigned cha
     constexpr bool kStage = !KNOTS;
     // this lane's chunk offsets in a ring stage (floats); word w = 3j + c of a round's
     // targets (and points) sits in chunk 1 + w / 4
-    const int o0 = 4 * (0 ^ swz), o1 = 4 * (1 ^ swz), o2 = 4 * (2 ^ swz), o3 = 4 * (3 ^ swz);
-    auto word = [&](int w) { return ((w < 4) ? o1 : (w < 8) ? o2 : o3) + (w & 3); };
+    const int kb = 4 * swz;
+    const int o1 = 4 * ((1 + swz) & 3), o2 = 4 * ((2 + swz) & 3), o3 = 4 * ((3 + swz) & 3);
+    auto word = [&](int w) { return (4 + w + kb) & 15; };   // target (point) word w of the round
     // one sample: span, basis, point, MSE and the adjoint accumulations
     // Samples past the lane's end (the last active lane's short tail, lanes without
     // samples) run the body too, as no-ops: every lane takes the same path, so the
@@ -346,7 +348,7 @@ __device__ __forceinline__ int curve_body(const KParams& kp, int t, unsigned cha
             float g[3];
 #pragma unroll
             for (int c = 0; c < 3; ++c) g[c] = rb[word(3 * j + c)];
-            process(bb + j, rb[o0 + j], g[0], g[1], g[2], rb, j, bb + j < b1);
+            process(bb + j, rb[(j + kb) & 15], g[0], g[1], g[2], rb, j, bb + j < b1);
         }
         if (kStage && has_pts) {   // sample j's targets were read before its point was written
             float* o = kp.pts + 3 * (it.pts + (long long)bb);

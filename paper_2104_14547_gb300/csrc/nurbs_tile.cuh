@@ -502,9 +502,10 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
     const int ioff = al16 ? 4 * lane : lane;
     const float* isrc = ring_on ? grow0 + 3LL * ra * it.nv + ioff : nullptr;
     const bool il16 = al16 && lane * 4 < nf;
-    auto issue_row = [&](int x) {
+    // row x into ring slot `slot` (row x's own slot, (x - ra) mod nring)
+    auto issue_row_at = [&](float* slot, int x) {
         if (ring_on && x < rb) {
-            float* d = ring + ((x - ra) & (nring - 1)) * 96 + ioff;
+            float* d = slot + ioff;
             if (al16) {
                 if (il16) cp_async16(d, isrc);
             } else {
@@ -514,6 +515,7 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
         cp_async_commit();
         isrc += 3 * it.nv;
     };
+    auto issue_row = [&](int x) { issue_row_at(ring + ((x - ra) & (nring - 1)) * 96, x); };
 
     // ---- staging, in three kinds of cp.async groups: the knot vectors and this tile's
     // samples (the tables below need only these), then the control net, then the first
@@ -969,9 +971,11 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
                 }
                 __syncwarp();
                 float4 lam[NR];
+                float* slot[NR];   // ring slots of rows r + q (refilled with rows r + q + nring)
 #pragma unroll
                 for (int q = 0; q < NR; ++q) {
-                    const float* gp = ring + ((r + q - ra) & (nring - 1)) * 96 + 3 * lane;
+                    slot[q] = ring + ((r + q - ra) & (nring - 1)) * 96;
+                    const float* gp = slot[q] + 3 * lane;
                     float gx, gy, gz;
                     float ginv = inv[q];   // dL/dS = ginv * W * (gx, gy, gz)
                     if constexpr (MSE) {
@@ -993,7 +997,7 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
                 }
                 __syncwarp();   // every lane has read these slots: refill them nring rows on
 #pragma unroll
-                for (int q = 0; q < NR; ++q) issue_row(r + q + nring);
+                for (int q = 0; q < NR; ++q) issue_row_at(slot[q], r + q + nring);
 #pragma unroll
                 for (int q = 0; q < NR; ++q)
 #pragma unroll
