@@ -1025,8 +1025,14 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
             while (r < rb) {
                 const int re = min(s_run[r], rb);
                 advance(s_su[r]);
-                for (; r + 1 < re; r += 2) step(IntTag<2>{}, r);
-                if (r < re) { step(IntTag<1>{}, r); ++r; }
+                // two-row steps, except where the knot cotangents of two rows (2 (P+1) > 8
+                // values) would push the step past its registers
+                if constexpr (!(KNOTS && P > 3)) {
+                    for (; r + 1 < re; r += 2) step(IntTag<2>{}, r);
+                    if (r < re) { step(IntTag<1>{}, r); ++r; }
+                } else {
+                    for (; r < re; ++r) step(IntTag<1>{}, r);
+                }
             }
         }
         if constexpr (GRAD) {
