@@ -173,3 +173,15 @@ def test_planner_tile_count_follows_the_tiling_rule(warps, rows):
     want = 2 + sum(max(1, -(-ns // (32 * warps))) for ns in (700, 0))
     assert lib.nurbs_plan_tiles(h) == want
     lib.nurbs_plan_destroy(h)
+
+
+def test_build_compiles_every_tile_kernel_once():
+    # k_tiles.cu is compiled once per (u degree, variant) pair; every other .cu once
+    jobs = _lib._jobs()
+    tiles = sorted(tuple(x for x in extra) for src, _, extra in jobs if src.endswith("k_tiles.cu"))
+    assert tiles == sorted((f"-DNURBS_P={p}", f"-DNURBS_V={v}") for p in range(6) for v in range(6))
+    objs = [o for _, o, _ in jobs]
+    assert len(objs) == len(set(objs))
+    others = {os.path.basename(src) for src, _, extra in jobs if not extra}
+    cu = {f for f in os.listdir(os.path.dirname(jobs[0][0])) if f.endswith(".cu")} - {"k_tiles.cu"}
+    assert others == cu
