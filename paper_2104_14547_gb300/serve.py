@@ -26,7 +26,12 @@ wave holds at most one request per model and as many evaluations as the output
 region has room for; requests that do not fit wait for the next wave.  Each wave
 is one libnurbs plan per kind (eval / fit) launched on its own stream; up to two
 waves are in flight at once, so requests that arrive while a wave runs start on
-the device before it finishes.  The plans bind to workspaces kept in a pool (one
+the device before it finishes.  A finished wave's evaluation results are copied
+into the requests' host arrays by the scheduler itself when the wave is small,
+and by a small pool of copy threads when it is large (under heavy load the
+copies, not the scheduling, bound the served request rate; handing a small wave
+to another thread costs more latency than its copy), while the scheduler forms
+and launches the next waves.  The plans bind to workspaces kept in a pool (one
 per wave slot and kind, grown when a wave needs more), so forming a wave
 allocates no device memory.  Every request records its latency (submit to result
 on the host).
@@ -34,6 +39,8 @@ on the host).
 from __future__ import annotations
 
 import collections
+import concurrent.futures
+import os
 import threading
 import time
 from dataclasses import dataclass, field
@@ -122,7 +129,7 @@ class Request:
 
 class Server:
     def __init__(self, device="cuda", hbm_fraction=0.25, max_wave=256, out_points=1 << 24, lr=1e-3,
-                 warps=4, rows=32, max_models=1 << 14):
+                 warps=4, rows=32, max_models=1 << 14, copy_workers=None, inline_copy_points=1 << 18):
         self.device = torch.device(device)
         if self.device.index is None:
             self.device = torch.device("cuda", torch.cuda.current_device())
@@ -166,6 +173,12 @@ class Server:
         self.waves = 0
         self.points_done = 0
         self.failure: str | None = None
+        # result copies of finished waves: a thread pool, and per wave slot the copies
+        # still reading that slot's pinned host buffer
+        self.copy_workers = copy_workers or max(1, min(8, os.cpu_count() or 1))
+        self.inline_copy_points = inline_copy_points   # waves with fewer evaluated points copy inline
+        self._copy_pool = None
+        self._copies = [[], []]
 
     # ------------------------------------------------------------ models
     def register(self, surface, target_pts: np.ndarray) -> int | None:
@@ -214,6 +227,8 @@ class Server:
 
     def start(self):
         self.running = True
+        self._copy_pool = concurrent.futures.ThreadPoolExecutor(max_workers=self.copy_workers,
+                                                                thread_name_prefix="nurbs-serve-copy")
         self.thread = threading.Thread(target=self._loop, daemon=True)
         self.thread.start()
 
@@ -223,6 +238,9 @@ class Server:
             self.cv.notify()
         if self.thread is not None:
             self.thread.join()
+        if self._copy_pool is not None:
+            self._copy_pool.shutdown(wait=True)
+            self._copy_pool = None
 
     def _form_wave(self, busy: set):
         """Pending requests admitted into one wave (arrival order, one per model,
@@ -294,6 +312,11 @@ class Server:
     def _launch(self, slot, evals, fits):
         se, sf = self.streams[slot]
         main = torch.cuda.current_stream(self.device)
+        # the copies of the slot's previous wave must be done reading its pinned buffer
+        # before this wave's results are copied into it
+        for f in self._copies[slot]:
+            f.result()
+        self._copies[slot] = []
         # plans first: their tables are uploaded into the pooled workspaces on the current stream
         pe = self._plan(slot, "eval", self._descs(evals, False)) if evals else None
         pf = self._plan(slot, "fit", self._descs(fits, True)) if fits else None
@@ -320,21 +343,45 @@ class Server:
         ev2.record(sf)
         return dict(slot=slot, evals=evals, fits=fits, plans=plans, events=(ev, ev2), n_out=n_out)
 
+    @staticmethod
+    def _deliver(ho, entries, shapes):
+        """Copy finished evaluations out of a wave's pinned buffer into their requests
+        and complete them (runs on a copy thread)."""
+        for (r, off), (nu, nv) in zip(entries, shapes):
+            try:
+                n = nu * nv
+                src = ho[off: off + n]
+                if r.out is not None:        # the caller's own buffer: no allocation here
+                    np.copyto(r.out.reshape(-1, 3)[:n], src)
+                    r.result = r.out
+                else:
+                    r.result = src.reshape(nu, nv, 3).copy()
+            except Exception as exc:  # the request fails, the server goes on
+                r.error = f"result copy failed: {exc!r}"
+            r.t_done = time.perf_counter()
+            r.done.set()
+
     def _complete(self, w, busy: set):
         for e in w["events"]:
             e.synchronize()
         now = time.perf_counter()
         ho = self.host_out[w["slot"]].numpy()
-        for r, off in w["evals"]:
-            m = self.models[r.model]
-            n = m.nu * m.nv
-            src = ho[off: off + n]
-            if r.out is not None:        # the caller's own buffer: no allocation here
-                np.copyto(r.out.reshape(-1, 3)[:n], src)
-                r.result = r.out
-            else:
-                r.result = src.reshape(m.nu, m.nv, 3).copy()
-            self.points_done += n
+        evals = w["evals"]
+        shapes = [(self.models[r.model].nu, self.models[r.model].nv) for r, _ in evals]
+        for r, _ in evals:
+            busy.discard(r.model)        # the device side of the wave is done
+        npts = sum(nu * nv for nu, nv in shapes)
+        self.points_done += npts
+        if evals and npts <= self.inline_copy_points:
+            self._deliver(ho, evals, shapes)
+        elif evals:
+            # split the copies over the pool in contiguous chunks of about equal bytes
+            k = min(self.copy_workers, len(evals))
+            cum = np.cumsum([nu * nv for nu, nv in shapes])
+            cuts = np.searchsorted(cum, cum[-1] * np.arange(1, k) / k) + 1
+            bounds = [0, *sorted(set(int(c) for c in cuts if 0 < c < len(evals))), len(evals)]
+            for a, b in zip(bounds[:-1], bounds[1:]):
+                self._copies[w["slot"]].append(self._copy_pool.submit(self._deliver, ho, evals[a:b], shapes[a:b]))
         hl = self.host_loss[w["slot"]].numpy()
         for k, r in enumerate(w["fits"]):
             m = self.models[r.model]
@@ -342,10 +389,6 @@ class Server:
             self._mt[r.model, 12] = m.steps
             r.result = float(hl[k]) / (3.0 * m.nu * m.nv)
             self.points_done += m.nu * m.nv
-        for r, _ in w["evals"]:
-            busy.discard(r.model)
-            r.t_done = now
-            r.done.set()
         for r in w["fits"]:
             busy.discard(r.model)
             r.t_done = now
