@@ -89,9 +89,9 @@ typedef struct nurbs_tile_cfg {
     int32_t warps;       /* warps per CTA (1..8; default 8) */
     int32_t ctas_per_sm; /* persistent CTAs per SM (0 = as many as fit).  k >= 2 also sizes the
                             shared memory of the gradient kernels so that k CTAs fit on an SM:
-                            fewer rows of dL/dS in flight per warp, then single-tile items whose
-                            adjoint no longer fits in shared memory reduce it through the
-                            workspace, then no staged control net.  Results are the same. */
+                            single-tile items whose adjoint no longer fits in shared memory
+                            reduce it through the workspace, then no staged control net.
+                            Results are the same. */
     int32_t max_ctas;    /* cap on the CTAs of each launch (0 = none); lets plans share the GPU */
 } nurbs_tile_cfg;
 

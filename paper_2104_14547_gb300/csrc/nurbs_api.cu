@@ -66,14 +66,13 @@ struct nurbs_plan {
     int64_t points;
     // shared memory carve-up
     int R, C, acc_cap;
-    int off_misc, off_su, off_u, off_nu, off_sv, off_v, off_nv, off_stage, off_beta, off_duc, off_dvc, off_ring,
+    int off_misc, off_su, off_u, off_nu, off_sv, off_v, off_nv, off_stage, off_beta, off_duc, off_dvc,
         off_jb, off_win, off_run, off_knots, off_w, off_acc, off_sa, off_dnu;
     int smem_bytes;           // gradient kernels
     int smem_eval;            // forward kernels (no shared adjoint)
     int smem_der;             // forward with tangents (derivative tables where the adjoint would be)
     int c_mc, c_wbytes, c_smem;   // curve kernels: control capacity, bytes per warp, per CTA
     int c_wbytes_f, c_smem_f;     // the same for the forward-only curve kernels
-    int ring_rows;                // rows of dL/dS (or target) in flight per warp (8 or 4)
     int win_cap;                  // largest control net staged in shared memory (0: none)
     float knot_sigma;             // smoothed-indicator knot derivative bandwidth (0: off)
     int grad_homog;               // control-point gradients with respect to Pw
@@ -291,11 +290,10 @@ nurbs_status nurbs_plan_create(int32_t kind, const nurbs_desc* h_desc, int32_t c
     // Shared memory carve-up for the largest tile, given the rows of dL/dS (or target)
     // in flight per warp, the largest staged control net and the largest shared adjoint
     // (single-tile items whose adjoint exceeds it use the workspace instead).
-    auto carve = [&](int ring_rows, int win_cap, size_t sa_cap) {
+    auto carve = [&](int win_cap, size_t sa_cap) {
         for (ItemDev& it : pl->items)
             it.smemA = (!it.ck && it.ntiles == 1 &&
                         smem_adjoint_bytes(it, pl->tiles[it.first_tile].nwr) <= sa_cap) ? 1 : 0;
-        pl->ring_rows = ring_rows;
         pl->win_cap = win_cap;
         size_t off = 0;
         auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 16); return (int)o; };
@@ -312,7 +310,6 @@ nurbs_status nurbs_plan_create(int32_t kind, const nurbs_desc* h_desc, int32_t c
         // column cotangents: one row of kv per (row group, column) of a tile; a tile has at
         // most as many (row group, column) pairs as its warps have lanes
         pl->off_dvc = take(4 * (size_t)max_unit_cols * kv);
-        pl->off_ring = take(4 * NW * ring_rows * 96);   // only the grad kernels use it
         pl->off_jb = take(8 * kJbCap);
         pl->off_win = take(16 * (size_t)win_cap);
         pl->off_run = take(4 * maxR);
@@ -333,21 +330,20 @@ nurbs_status nurbs_plan_create(int32_t kind, const nurbs_desc* h_desc, int32_t c
         pl->acc_cap = (int)(off - pl->off_acc);
         pl->smem_bytes = (int)off;
     };
-    carve(kRing, kWinCap, kSmemACap);
+    carve(kWinCap, kSmemACap);
     // A plan asked for k >= 2 persistent CTAs per SM gets a carve-up that lets k gradient
     // CTAs share an SM (228 KB of shared memory per SM, 1 KB of it reserved per CTA):
-    // first half the rows in flight per warp, then a smaller shared adjoint, then no
-    // staged control net (the kernels then read control points from global memory).
+    // first a smaller shared adjoint, then no staged control net (the kernels then read
+    // control points from global memory).
     if (pl->ctas_per_sm >= 2) {
         const size_t budget = (size_t)kSmemPerSM / pl->ctas_per_sm - 1024;
-        auto fit_sa = [&](int ring_rows, int win_cap) {
-            carve(ring_rows, win_cap, 0);
+        auto fit_sa = [&](int win_cap) {
+            carve(win_cap, 0);
             const size_t rest = (size_t)pl->smem_bytes;
-            carve(ring_rows, win_cap, rest < budget ? std::min<size_t>(budget - rest, kSmemACap) : 0);
+            carve(win_cap, rest < budget ? std::min<size_t>(budget - rest, kSmemACap) : 0);
         };
-        if ((size_t)pl->smem_bytes > budget) carve(kRing / 2, kWinCap, kSmemACap);
-        if ((size_t)pl->smem_bytes > budget) fit_sa(kRing / 2, kWinCap);
-        if ((size_t)pl->smem_bytes > budget) fit_sa(kRing / 2, 0);
+        if ((size_t)pl->smem_bytes > budget) fit_sa(kWinCap);
+        if ((size_t)pl->smem_bytes > budget) fit_sa(0);
     }
     // workspace layout
     size_t w = kHeaderBytes;
@@ -494,7 +490,7 @@ void fill_tables(KParams& kp, const nurbs_plan* pl, unsigned char* ws)
     kp.R = pl->R; kp.C = pl->C;
     kp.off_misc = pl->off_misc; kp.off_su = pl->off_su; kp.off_u = pl->off_u; kp.off_nu = pl->off_nu;
     kp.off_sv = pl->off_sv; kp.off_v = pl->off_v; kp.off_nv = pl->off_nv; kp.off_stage = pl->off_stage;
-    kp.off_beta = pl->off_beta; kp.off_duc = pl->off_duc; kp.off_dvc = pl->off_dvc; kp.off_ring = pl->off_ring;
+    kp.off_beta = pl->off_beta; kp.off_duc = pl->off_duc; kp.off_dvc = pl->off_dvc;
     kp.off_jb = pl->off_jb; kp.off_win = pl->off_win; kp.off_run = pl->off_run;
     kp.off_knots = pl->off_knots; kp.off_w = pl->off_w; kp.off_sa = pl->off_sa; kp.off_acc = pl->off_acc;
     kp.off_dnu = pl->off_dnu;
@@ -502,7 +498,6 @@ void fill_tables(KParams& kp, const nurbs_plan* pl, unsigned char* ws)
     kp.c_mc = pl->c_mc;
     kp.c_wbytes = pl->c_wbytes;
     kp.knot_sigma = pl->knot_sigma;
-    kp.ring_rows = pl->ring_rows;
     kp.win_cap = pl->win_cap;
     kp.grad_homog = pl->grad_homog;
 }

@@ -39,7 +39,6 @@ enum : unsigned {
     kErrOrder = 1u << 5,
 };
 
-constexpr int kRing = 8;        // rows of dL/dS (or target) in flight per warp (the default; a plan may use kRing / 2)
 constexpr int kBatch = 4;       // retired control rows contracted together
 constexpr int kJbCap = 256;     // column ranges cached per tile
 constexpr int kWinCap = 1024;   // control points staged in shared memory (whole net, else the tile's window)
@@ -71,7 +70,7 @@ struct KParams {
     int step;                // Adam step of the launch (items may override)
     // shared-memory carve-up in bytes (host-computed for the plan's largest tile)
     int R, C;
-    int off_misc, off_su, off_u, off_nu, off_sv, off_v, off_nv, off_stage, off_beta, off_duc, off_dvc, off_ring,
+    int off_misc, off_su, off_u, off_nu, off_sv, off_v, off_nv, off_stage, off_beta, off_duc, off_dvc,
         off_jb, off_win, off_run, off_knots, off_w, off_acc, off_sa, off_dnu;
 
     int acc_cap;             // bytes available to the final reduction from off_acc
@@ -81,7 +80,6 @@ struct KParams {
     int c_mc, c_wbytes;      // curve kernels: control-point capacity, shared bytes per warp
     float knot_sigma;        // > 0: knot derivative with the Gaussian-smoothed indicator term
     int grad_homog;          // grad_ctrl receives dL/dPw (homogeneous) instead of dL/d(P, w)
-    int ring_rows;           // rows of dL/dS (or target) in flight per warp: kRing or kRing / 2
     int win_cap;             // control points staged in shared memory at most (0: none)
 };
 
@@ -485,41 +483,12 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
     const int bl = wcol0 + lane;
     const int blc = min(bl, max(ncols - 1, 0));
 
-    // ring of incoming dL/dS (or target) rows for this warp's columns; the first
-    // rows are requested before the prologue so their latency overlaps it
-    const int nring = kp.ring_rows;   // a power of two
-    float* ring = reinterpret_cast<float*>(smem + kp.off_ring) + warp * (nring * 96);
-    const int nf = 3 * nvw;
     const long long prow0 = it.pts + (long long)tl.row0 * it.nv + tl.col0 + wcol0;  // point (row 0, lane 0)
     const float* grow0 = GRAD ? kp.gin + 3 * prow0 : nullptr;
-    const bool al16 = ((prow0 & 3) == 0) && ((it.nv & 3) == 0) && ((nvw & 3) == 0);
     const bool wrows = !empty && wr < nwr && ra < rb;
-    // Requests go out in row order, one commit group per row (empty past the unit's
-    // rows): the first nring rows before the prologue, then each step refills the
-    // slots it has just read with the rows nring further on.  Row x sits in slot
-    // (x - ra) mod nring.
-    const bool ring_on = wrows && nf > 0;
-    const int ioff = al16 ? 4 * lane : lane;
-    const float* isrc = ring_on ? grow0 + 3LL * ra * it.nv + ioff : nullptr;
-    const bool il16 = al16 && lane * 4 < nf;
-    // row x into ring slot `slot` (row x's own slot, (x - ra) mod nring)
-    auto issue_row_at = [&](float* slot, int x) {
-        if (ring_on && x < rb) {
-            float* d = slot + ioff;
-            if (al16) {
-                if (il16) cp_async16(d, isrc);
-            } else {
-                for (int k = 0; lane + k < nf; k += 32) cp_async4(d + k, isrc + k);
-            }
-        }
-        cp_async_commit();
-        isrc += 3 * it.nv;
-    };
-    auto issue_row = [&](int x) { issue_row_at(ring + ((x - ra) & (nring - 1)) * 96, x); };
-
-    // ---- staging, in three kinds of cp.async groups: the knot vectors and this tile's
-    // samples (the tables below need only these), then the control net, then the first
-    // rows of the ring.  The tables are built while the net and the ring rows land.
+    // ---- staging, in two cp.async groups: the knot vectors and this tile's samples (the
+    // tables below need only these), then the control net.  The tables are built while
+    // the net and the first dL/dS (or target) rows land.
     float* s_knU = reinterpret_cast<float*>(smem + kp.off_knots);
     float* s_knV = s_knU + ((P > 0) ? ((it.n1 + P + 1 + 3) & ~3) : 0);
     const int nU = (P > 0) ? it.n1 + P + 1 : 0, nV = it.m1 + Q + 1;
@@ -542,12 +511,33 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
             cp_async16(reinterpret_cast<float*>(s_win + e), reinterpret_cast<const float*>(src + e));
     }
     cp_async_commit();
+    // dL/dS (or target) rows come straight from global memory into registers: each step
+    // loads the two rows after its own and prefetches the two after those into L2 (a
+    // shared-memory ring cost more instructions per row than the loads)
+    const bool pf_on = GRAD && wrows && lane < nvw;
+    const float* psrc = pf_on ? grow0 + 3 * lane : nullptr;   // tile row 0, this lane's point
+    auto load_row = [&](int x, float (&v)[3]) {
+        if (pf_on && x < rb) {
+            const float* p = psrc + (long long)x * (3 * it.nv);
+            v[0] = __ldcs(p); v[1] = __ldcs(p + 1); v[2] = __ldcs(p + 2);
+        } else {
+            v[0] = v[1] = v[2] = 0.f;
+        }
+    };
+    auto prefetch_row = [&](int x) {
+        if (pf_on && x < rb) {
+            const float* p = psrc + (long long)x * (3 * it.nv);
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+        }
+    };
+    float pf0[3], pf1[3];
     if constexpr (GRAD) {
-        for (int d = 0; d < nring; ++d) issue_row(ra + d);
-        if (nring == kRing) cp_async_wait<kRing + 1>(); else cp_async_wait<kRing / 2 + 1>();
-    } else {
-        cp_async_wait<1>();
+        load_row(ra, pf0);
+        load_row(ra + 1, pf1);
+        prefetch_row(ra + 2);
+        prefetch_row(ra + 3);
     }
+    cp_async_wait<1>();
     __syncthreads();
 
     // ---- one pass over rows and columns: device checks (knot vectors once per item,
@@ -714,12 +704,8 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
     }
     if (win_only) {
         cp_async_wait<0>();
-    } else if (net_staged) {   // the net's group; only the ring rows may still be in flight
-        if constexpr (GRAD) {
-            if (nring == kRing) cp_async_wait<kRing>(); else cp_async_wait<kRing / 2>();
-        } else {
-            cp_async_wait<0>();
-        }
+    } else if (net_staged) {   // the net's group
+        cp_async_wait<0>();
     }
     __syncthreads();
     if (win) {
@@ -902,7 +888,7 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
         float* s_beta_w = reinterpret_cast<float*>(smem + kp.off_beta) + (wc * kp.R) * SU;
 
         // One or two rows (same u-span) per step: S, dL/dS, lambda, tau and beta.
-        // NR = rows in the step; the ring slots of rows < r are free for refills.
+        // NR = rows in the step; its dL/dS (or target) rows are in pf0 / pf1 on entry.
         auto step = [&](auto nr_tag, int r) {
             constexpr int NR = decltype(nr_tag)::value;
             float Nu[NR][PB];
@@ -963,19 +949,25 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
                     }
                 }
             } else {
-                // rows r .. r+nring-1 are in flight, one group each: wait for the first NR
-                if (nring == kRing) {
-                    if constexpr (NR == 2) cp_async_wait<kRing - 2>(); else cp_async_wait<kRing - 1>();
+                float gv[NR][3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) gv[0][c] = pf0[c];
+                if constexpr (NR == 2) {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) gv[1][c] = pf1[c];
+                    load_row(r + 2, pf0);
+                    load_row(r + 3, pf1);
                 } else {
-                    if constexpr (NR == 2) cp_async_wait<kRing / 2 - 2>(); else cp_async_wait<kRing / 2 - 1>();
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) pf0[c] = pf1[c];
+                    load_row(r + 2, pf1);
                 }
-                __syncwarp();
+                prefetch_row(r + 4);
+                prefetch_row(r + 5);
                 float4 lam[NR];
-                float* slot[NR];   // ring slots of rows r + q (refilled with rows r + q + nring)
 #pragma unroll
                 for (int q = 0; q < NR; ++q) {
-                    slot[q] = ring + ((r + q - ra) & (nring - 1)) * 96;
-                    const float* gp = slot[q] + 3 * lane;
+                    const float* gp = gv[q];
                     float gx, gy, gz;
                     float ginv = inv[q];   // dL/dS = ginv * W * (gx, gy, gz)
                     if constexpr (MSE) {
@@ -995,9 +987,6 @@ __device__ __forceinline__ void tile_body(const KParams& kp, int t)
                     const float gbx = gx * ginv, gby = gy * ginv, gbz = gz * ginv;
                     lam[q] = make_float4(gbx, gby, gbz, -fmaf(Sx[q], gbx, fmaf(Sy[q], gby, Sz[q] * gbz)));
                 }
-                __syncwarp();   // every lane has read these slots: refill them nring rows on
-#pragma unroll
-                for (int q = 0; q < NR; ++q) issue_row_at(slot[q], r + q + nring);
 #pragma unroll
                 for (int q = 0; q < NR; ++q)
 #pragma unroll

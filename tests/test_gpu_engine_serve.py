@@ -334,10 +334,17 @@ def test_server_eval_into_caller_buffer():
 
 
 def test_two_ctas_per_sm_carve_up_same_results():
-    # degree-5 items up to 256 samples wide need more shared memory than two 8-warp CTAs
-    # can share; a plan asked for 2 CTAs per SM trims its carve-up (fewer target rows in
-    # flight, adjoints through the workspace, no staged net) and gives the same results
-    surfs, tg = synth.ragged_batch(52, batch=10, deg=(5, 5), net=(30, 48), grid=(180, 256))
+    # single-tile degree-5 items 225 to 256 samples wide with 36..44-point nets: their
+    # tables and shared adjoints need more shared memory than two 8-warp CTAs can share;
+    # a plan asked for 2 CTAs per SM trims its carve-up (adjoints through the workspace,
+    # then no staged net) and gives the same results
+    rng = np.random.default_rng(52)
+    surfs, tg = [], []
+    for _ in range(10):
+        n1, m1 = (int(x) for x in rng.integers(36, 45, size=2))
+        s = synth.surface(rng, 5, 5, n1, m1, int(rng.integers(96, 129)), int(rng.integers(225, 257)))
+        surfs.append(s)
+        tg.append(synth.twin_net(rng, s))
     T = np.concatenate([O.surface_eval(t.p, t.q, t.U, t.V, t.ctrl, t.u, t.v).reshape(-1, 3) for t in tg])
     pk = batch.pack_surfaces(surfs)
     kn, ct, pr = batch.to_device(pk)
