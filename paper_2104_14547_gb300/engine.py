@@ -58,11 +58,13 @@ class RaggedEngine:
         sms = torch.cuda.get_device_properties(self.device).multi_processor_count
         op = "mse_knots" if knots_grad else "mse"
         assert budget in ("warps", "occupancy", "none")
-        # degree groups
+        # degree groups, launched heaviest first (points times the (p+1)(q+1) terms of
+        # each point) so that the groups with the longest tiles do not start last
         keys = sorted(set(zip(pk.descs["p"].tolist(), pk.descs["q"].tolist())))
         work = {k: 0 for k in keys}
         for d in pk.descs:
             work[(int(d["p"]), int(d["q"]))] += int(d["nu"]) * int(d["nv"]) + 1
+        keys.sort(key=lambda k: -work[k] * (k[0] + 1) * (k[1] + 1))
         total = sum(work.values())
         self._cap_fns = {}
         tuned = {}
