@@ -228,6 +228,9 @@ nurbs_status nurbs_plan_create(int32_t kind, const nurbs_desc* h_desc, int32_t c
             int R = it.curve ? 1 : (rows_cfg > 0 ? rows_cfg : 16 * nwr);
             nwr = std::min(nwr, R);
             const int nrt = std::max(1, (it.nu + R - 1) / R);
+            // row tiles of equal height (an item's tiles run side by side, so its longest
+            // tile sets when it is done)
+            const int Rb = std::max(1, (it.nu + nrt - 1) / nrt);
             it.rcap = it.n1;
             it.ku_cap = it.curve ? 0 : it.n1 + it.p + 1;
             it.kv_cap = it.m1 + it.q + 1;
@@ -240,8 +243,8 @@ nurbs_status nurbs_plan_create(int32_t kind, const nurbs_desc* h_desc, int32_t c
                     TileDev tl;
                     std::memset(&tl, 0, sizeof tl);
                     tl.item = k;
-                    tl.row0 = rt * R;
-                    tl.nrows = std::max(0, std::min(R, it.nu - tl.row0));
+                    tl.row0 = rt * Rb;
+                    tl.nrows = std::max(0, std::min(Rb, it.nu - tl.row0));
                     tl.col0 = ct * cw;
                     tl.ncols = std::max(0, std::min(cw, it.nv - tl.col0));
                     tl.tidx = ntl++;
