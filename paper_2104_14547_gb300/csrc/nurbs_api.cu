@@ -439,6 +439,11 @@ KernelVariant variant_for(int v, int p, int q)
 #undef NURBS_TILE_V
 }
 
+// Dynamic shared memory a kernel launches with before its limit must be raised: the
+// 48 KB default covers static and dynamic shared memory together, and the kernels'
+// static shared memory is a few bytes, so the attribute is raised above 47 KB.
+constexpr int kSmemNoOptin = 47 * 1024;
+
 // Kernel, block, shared memory and queue slot of one group for variant v.
 struct GroupLaunch {
     KernelVariant kv;
@@ -463,7 +468,7 @@ nurbs_status size_group(nurbs_plan* pl, PlanGroup& grp, int v, const GroupLaunch
     // the attribute is per kernel function: raise it to the device limit so that
     // no plan lowers it under another plan's launch size
     cudaError_t e = cudaSuccess;
-    if (gl.smem > 48 * 1024) {
+    if (gl.smem > kSmemNoOptin) {
         int limit = 0;
         e = gl.kv.set_smem(&limit);
         if (e == cudaSuccess && gl.smem > limit) return NURBS_ERR_SIZE;
@@ -556,7 +561,7 @@ nurbs_status nurbs_plan_occupancy(const nurbs_plan* plan, int32_t op, int32_t* c
     for (const PlanGroup& grp : plan->groups) {
         const GroupLaunch gl = group_launch(plan, grp, op);
         cudaError_t e = cudaSuccess;
-        if (gl.smem > 48 * 1024) {
+        if (gl.smem > kSmemNoOptin) {
             int limit = 0;
             e = gl.kv.set_smem(&limit);
             if (e == cudaSuccess && gl.smem > limit) return NURBS_ERR_SIZE;

@@ -372,3 +372,37 @@ def test_two_ctas_per_sm_carve_up_same_results():
         _, g = O.mse(ref, Tk[k].astype(np.float64), 3 * pk.npts)
         rc, _, _ = O.surface_vjp(s.p, s.q, s.U, s.V, s.ctrl, s.u, s.v, g)
         assert rel_inf(dc[k], rc) <= G_TOL
+
+
+def test_plan_at_the_48k_shared_memory_edge_launches():
+    # a serving wave's fit plan whose carve-up came to exactly 48 KB: with the kernels'
+    # few bytes of static shared memory that is over the default per-block limit, so the
+    # kernel's limit must be raised before launch (a wave like this once failed with
+    # "item exceeds a kernel limit")
+    rng = np.random.default_rng(61)
+    surfs = [synth.surface(rng, 4, 3, 45, 40, 221, 200), synth.surface(rng, 4, 5, 58, 8, 110, 114)]
+    tg = [synth.twin_net(rng, s) for s in surfs]
+    T = np.concatenate([O.surface_eval(t.p, t.q, t.U, t.V, t.ctrl, t.u, t.v).reshape(-1, 3) for t in tg])
+    pk = batch.pack_surfaces(surfs)
+    kn, ct, pr = batch.to_device(pk)
+    Td = torch.from_numpy(T.astype(np.float32)).cuda()
+    plan = batch.Plan.for_packed(pk, warps=4, rows=32)
+    for op in ("eval", "mse", "mse_knots"):
+        assert plan.occupancy(op)[0] >= 1, op
+    pts, gc, gk = torch.empty_like(Td), torch.empty_like(ct), torch.empty_like(kn)
+    loss = torch.empty(pk.count, device="cuda")
+    plan.mse_fwd_bwd(kn, ct, pr, Td, pts, gc, gk, loss, 2.0 / (3 * pk.npts))
+    m, v = torch.zeros_like(ct), torch.zeros_like(ct)
+    ct2 = ct.clone()
+    plan.fit_step(kn, ct2, pr, Td, m, v, 1, loss_items=loss)
+    torch.cuda.synchronize()
+    assert plan.get_error()[0] == 0
+    S = batch.unpack_points(pk, pts.cpu().numpy())
+    dc = batch.unpack_ctrl(pk, gc.cpu().numpy())
+    Tk = batch.unpack_points(pk, T)
+    for k, s in enumerate(surfs):
+        ref = O.surface_eval(s.p, s.q, s.U, s.V, s.ctrl, s.u, s.v)
+        assert np.abs(S[k] - ref).max() <= S_TOL * bbox_diag(s.ctrl)
+        _, g = O.mse(ref, Tk[k].astype(np.float64), 3 * pk.npts)
+        rc, _, _ = O.surface_vjp(s.p, s.q, s.U, s.V, s.ctrl, s.u, s.v, g)
+        assert rel_inf(dc[k], rc) <= G_TOL
