@@ -51,6 +51,18 @@ import torch
 from . import _lib, batch
 
 
+def copy_chunks(sizes, workers: int):
+    """Bounds [0, b1, ..., len(sizes)] that cut a wave's evaluations into at most
+    `workers` contiguous chunks of about equal total size (in points), none empty."""
+    n = len(sizes)
+    if n == 0:
+        return [0]
+    k = max(1, min(workers, n))
+    cum = np.cumsum(np.asarray(sizes, dtype=np.int64))
+    cuts = np.searchsorted(cum, cum[-1] * np.arange(1, k) / k) + 1
+    return [0, *sorted(set(int(c) for c in cuts if 0 < c < n)), n]
+
+
 class RangeAllocator:
     """First-fit free list over [0, size) (units: elements)."""
 
@@ -375,11 +387,7 @@ class Server:
         if evals and npts <= self.inline_copy_points:
             self._deliver(ho, evals, shapes)
         elif evals:
-            # split the copies over the pool in contiguous chunks of about equal bytes
-            k = min(self.copy_workers, len(evals))
-            cum = np.cumsum([nu * nv for nu, nv in shapes])
-            cuts = np.searchsorted(cum, cum[-1] * np.arange(1, k) / k) + 1
-            bounds = [0, *sorted(set(int(c) for c in cuts if 0 < c < len(evals))), len(evals)]
+            bounds = copy_chunks([nu * nv for nu, nv in shapes], self.copy_workers)
             for a, b in zip(bounds[:-1], bounds[1:]):
                 self._copies[w["slot"]].append(self._copy_pool.submit(self._deliver, ho, evals[a:b], shapes[a:b]))
         hl = self.host_loss[w["slot"]].numpy()
