@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 import torch
 
-from gpu_util import G_TOL, S_TOL, bbox_diag, check_points, gpu_eval, oracle_eval, oracle_vjp, pack, rel_inf
+from gpu_util import G_TOL, check_points, gpu_eval, oracle_eval, oracle_vjp, pack, rel_inf
 from oracle import oracle as O
 from paper_2104_14547_gb300 import _lib, batch, synth
 

@@ -3,7 +3,6 @@ gradients (Eq. 7, Eq. 8, Eq. 9 and the knot derivative of Sec. 3.2), the MSE los
 and the Adam step, against facts fixed by geometry, by library routines and by
 central finite differences."""
 import json
-import math
 import os
 
 import numpy as np
